@@ -1,0 +1,175 @@
+/*
+ * smre.h -- C ABI of the GB300 (sm_103a) statistical multi-resolution
+ * projection library, libsmre.so.
+ *
+ * What it computes (arXiv 1503.03492):
+ *   Given a residual image x0 (H x W, row-major) and a scale set of square
+ *   window sides, project x0 onto the intersection of the convex sets
+ *       C_s = { v : sum_{i in s} v_i^2 <= cS(|s|) }
+ *   one per L x L window s of every side L in the set at every position fully
+ *   inside the image (Sec. 2, Eqs. tau_s, tau_G; the projection P_G of
+ *   Sec. 2.2).  cS = 1 / c_s(alpha) is the bound of Sec. 2.1.
+ *   - smre_dykstra_project runs Dykstra's cyclic projection (Sec. 2.3,
+ *     Algorithm 2) to a stopping tolerance or a cycle cap;
+ *   - smre_dykstra_project_incomplete runs the incomplete Dykstra variant of
+ *     Sec. 3.2 (dyadic squares, passes at shifts 2^i).
+ *
+ * Conventions shared by every entry point:
+ *   - Errors are returned as smre_status codes; nothing aborts, nothing throws.
+ *     smre_last_error gives a one-line message for the last failure.
+ *   - Image pointers x0 / x may be host or device pointers (the library asks
+ *     the CUDA runtime which).  Host images are staged through device buffers
+ *     owned by the handle.  x may equal x0.  Pitch is always `width` floats.
+ *   - Work is enqueued on the CUDA stream given to smre_dykstra_create.  When
+ *     `res` is non-NULL the call waits for that stream and fills *res; when it
+ *     is NULL the call returns once the work is enqueued.
+ *   - The handle owns every device allocation (increments q_s, work copies of
+ *     x, reduction scratch); none is freed before smre_dykstra_destroy.
+ *   - A handle is not thread-safe: one host thread at a time per handle.
+ */
+#ifndef SMRE_H
+#define SMRE_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define SMRE_API __attribute__((visibility("default")))
+#else
+#define SMRE_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct smre_dykstra smre_dykstra; /* opaque handle */
+
+typedef enum {
+    SMRE_OK = 0,
+    SMRE_EINVAL = 1,        /* bad argument; nothing was enqueued                 */
+    SMRE_ENOMEM = 2,        /* device or pinned host allocation failed            */
+    SMRE_ECUDA = 3,         /* a CUDA runtime call failed (message has the name)  */
+    SMRE_ETIMEOUT = 4,      /* a device-side wait ran out of its time limit       */
+    SMRE_ENOTCONVERGED = 5  /* cycle cap reached before the tolerance (tol >= 0);
+                               the result is still the valid last iterate         */
+} smre_status;
+
+/* How the bounds cS are chosen (Sec. 2.1).  With mu_s = (|s| - 1/2)^(1/4) and
+ * sigma_s^2 = 1 / (8 sqrt|s|), cS = (q sigma_s + mu_s)^4 where
+ *   PERSET   q = Phi^{-1}(alpha): the fourth-root normal approximation of the
+ *            per-window chi^2_{|s|} alpha-quantile (default);
+ *   MAXSTAT  q = Monte Carlo alpha-quantile of Q_Omega = max_s (t_s^(1/4) - mu_s)
+ *            / sigma_s on H x W images of iid N(0,1) noise;
+ * and
+ *   CHI2     cS = the exact chi^2_{|s|} alpha-quantile;
+ *   EXPLICIT cS = c_explicit[j] for sides[j]. */
+typedef enum {
+    SMRE_C_PERSET = 0,
+    SMRE_C_CHI2 = 1,
+    SMRE_C_MAXSTAT = 2,
+    SMRE_C_EXPLICIT = 3
+} smre_cmode;
+
+/* flags */
+#define SMRE_F_VIOLATION 1  /* fill smre_result.max_violation (one extra pass)   */
+
+typedef struct {
+    int height, width;          /* pixels: 1 <= height <= 65535, 1 <= width <= 4096 */
+    const int *sides;           /* n_sides window sides, 1 <= L <= min(H, W, 32);
+                                   duplicates are ignored                           */
+    int n_sides;
+    double alpha;               /* confidence, 0 < alpha < 1 (unused for EXPLICIT)  */
+    smre_cmode cmode;
+    const double *c_explicit;   /* n_sides bounds (EXPLICIT only), aligned with sides */
+    int max_cycles;             /* cycle cap of the standard method, >= 1           */
+    double tol;                 /* stopping tolerance; < 0: run exactly max_cycles  */
+    int tol_relative;           /* 0: |x_r - x_{r-1}|_2 <= tol;
+                                   1: |x_r - x_{r-1}|_2 <= tol |x_{r-1}|_2         */
+    int q_dtype;                /* increment storage: 0 = FP32 (only value so far)  */
+    int icd_max_sweeps;         /* per-tile sweep cap of the incomplete method (0: 1000) */
+    int maxstat_draws;          /* Monte Carlo draws for MAXSTAT (0: 1000)         */
+    unsigned long long seed;    /* seed of the MAXSTAT draws                        */
+    int flags;                  /* SMRE_F_* */
+} smre_params;
+
+typedef struct {
+    int cycles;                 /* standard: cycles run; incomplete: total sweeps of all tiles */
+    int status;                 /* smre_status of the run                          */
+    double step;                /* standard: |x_r - x_{r-1}|_2 of the last cycle   */
+    double rel_step;            /* step / |x_{r-1}|_2                              */
+    double max_violation;       /* max_s (|x_s|^2 - cS)/cS over all windows of the
+                                   scale set (<= 0: feasible); NaN unless requested */
+    long long windows;          /* window projections performed                    */
+    int max_tile_sweeps;        /* incomplete: largest per-tile sweep count        */
+    double seconds;             /* device time of the run (CUDA events)           */
+} smre_result;
+
+/* Bounds cS for p->sides (in that order) under p->cmode, computed on the host
+ * in FP64 (Sec. 2.1).  cS_out receives n_sides values.  MAXSTAT needs a CUDA
+ * device (the Monte Carlo draws run on it). */
+SMRE_API smre_status smre_bounds(const smre_params *p, double *cS_out);
+
+/* Validate p, compute the bounds, and allocate every device buffer a
+ * projection of an H x W image with these sides needs: the increments q_s of
+ * all sets (sum over L of L^2 * H * W FP32 values, padded rows), two work
+ * images and reduction scratch.  `cuda_stream` is a cudaStream_t (NULL: the
+ * legacy default stream).  On success *out owns all of it.
+ * Errors: EINVAL (bad parameters), ENOMEM, ECUDA. */
+SMRE_API smre_status smre_dykstra_create(const smre_params *p, void *cuda_stream, smre_dykstra **out);
+
+/* Dykstra's cyclic projection (Sec. 2.3, Algorithm 2): starting from q_s = 0,
+ * repeat cycles over every set in the fixed order (sides descending; for each
+ * side L the tilings (L, a, b), a outer, b inner, a, b in 0..L-1; windows of a
+ * tiling in parallel) with, per set, y = x + q_s, x = p_s(y) (Eq. dykstra:if),
+ * q_s = y - x, until the stopping test of the handle's parameters holds or
+ * max_cycles cycles ran.  x0, x: H x W float images (host or device).
+ * Returns OK, ENOTCONVERGED (cap hit, x valid), EINVAL, ETIMEOUT or ECUDA. */
+SMRE_API smre_status smre_dykstra_project(smre_dykstra *h, const float *x0, float *x, smre_result *res);
+
+/* Incomplete Dykstra (Sec. 3.2): with B = 2^K, passes i = 0..K cover the image
+ * with B x B tiles at origins (1 << i) mod B + B * t (tiles fully inside); in
+ * each tile, Dykstra's algorithm over the non-overlapping 2^k squares of
+ * levels k = K down to i, increments zeroed per tile and pass, repeated until
+ * the L1 change of one sweep is <= tol * B^2 (at least one sweep, at most
+ * icd_max_sweeps).  Bounds of side 2^k follow the handle's cmode (EXPLICIT
+ * and MAXSTAT: 2^k must be one of the handle's sides).  K < 0 means floor(log2 max side);
+ * 0 <= K <= 5.  Returns OK, EINVAL, ECUDA. */
+SMRE_API smre_status smre_dykstra_project_incomplete(smre_dykstra *h, const float *x0, float *x,
+                                            int K, double tol, smre_result *res);
+
+/* Change the stopping rule of the standard method for later calls. */
+SMRE_API smre_status smre_dykstra_set_stopping(smre_dykstra *h, int max_cycles, double tol,
+                                      int tol_relative);
+
+/* Bounds cS the handle uses for its sides, in ascending side order; n >= n_sides. */
+SMRE_API smre_status smre_dykstra_bounds(const smre_dykstra *h, int *sides_out, double *cS_out, int n);
+
+/* Per-cycle history of the last smre_dykstra_project call: out[2r] = step of
+ * cycle r+1, out[2r+1] = |x_r|_2 before it.  *n_cycles receives the count;
+ * at most n_max cycles are copied. */
+SMRE_API smre_status smre_dykstra_history(smre_dykstra *h, double *out, int n_max, int *n_cycles);
+
+/* Per-tile sweep counts of the last smre_dykstra_project_incomplete call,
+ * pass by pass (i = 0..K), tiles row-major within a pass.  *n_tiles receives
+ * the total; at most n_max values are copied. */
+SMRE_API smre_status smre_dykstra_icd_sweeps(smre_dykstra *h, int *out, int n_max, int *n_tiles);
+
+/* Bytes of device memory the handle holds. */
+SMRE_API size_t smre_dykstra_device_bytes(const smre_dykstra *h);
+
+/* Release every resource of the handle (NULL is allowed).  Waits for the
+ * handle's stream first. */
+SMRE_API void smre_dykstra_destroy(smre_dykstra *h);
+
+/* Message of the last failure on h, or of the last failed create / bounds
+ * call on this thread when h is NULL.  Never NULL. */
+SMRE_API const char *smre_last_error(const smre_dykstra *h);
+
+/* Library version string. */
+SMRE_API const char *smre_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SMRE_H */

@@ -1,0 +1,299 @@
+"""GB300 (sm_103a) statistical multi-resolution projection (arXiv 1503.03492).
+
+Thin ctypes binding of the C ABI in ``include/smre.h`` (``libsmre.so``).  The
+functions keep the C names; every step of the projection runs in the CUDA
+kernels of the library, this module only marshals arguments.  Images may be
+``torch`` CUDA tensors, ``torch`` CPU tensors or ``numpy`` arrays (float32,
+C-contiguous, H x W); CUDA tensors are passed by device pointer, host arrays
+by host pointer (the library stages them).
+
+The library must have been built (``python -m paper_1503_03492_gb300.build``
+or ``__graft_entry__.build()``); every call raises ImportError when it is
+missing.  There is no fallback of any kind.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+__all__ = [
+    "SMRE_OK", "SMRE_EINVAL", "SMRE_ENOMEM", "SMRE_ECUDA", "SMRE_ETIMEOUT", "SMRE_ENOTCONVERGED",
+    "SMRE_C_PERSET", "SMRE_C_CHI2", "SMRE_C_MAXSTAT", "SMRE_C_EXPLICIT", "SMRE_F_VIOLATION",
+    "SmreError", "smre_params", "smre_result", "lib_path", "load",
+    "smre_bounds", "smre_dykstra_create", "smre_dykstra_project",
+    "smre_dykstra_project_incomplete", "smre_dykstra_set_stopping", "smre_dykstra_bounds",
+    "smre_dykstra_history", "smre_dykstra_icd_sweeps", "smre_dykstra_device_bytes",
+    "smre_dykstra_destroy", "smre_last_error", "smre_version", "Projector", "EXPORTED",
+]
+
+SMRE_OK, SMRE_EINVAL, SMRE_ENOMEM, SMRE_ECUDA, SMRE_ETIMEOUT, SMRE_ENOTCONVERGED = range(6)
+SMRE_C_PERSET, SMRE_C_CHI2, SMRE_C_MAXSTAT, SMRE_C_EXPLICIT = range(4)
+SMRE_F_VIOLATION = 1
+
+_STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENOTCONVERGED"}
+
+# every entry point declared in include/smre.h
+EXPORTED = (
+    "smre_bounds", "smre_dykstra_create", "smre_dykstra_project",
+    "smre_dykstra_project_incomplete", "smre_dykstra_set_stopping", "smre_dykstra_bounds",
+    "smre_dykstra_history", "smre_dykstra_icd_sweeps", "smre_dykstra_device_bytes",
+    "smre_dykstra_destroy", "smre_last_error", "smre_version",
+)
+
+
+class SmreError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class smre_params(ctypes.Structure):
+    _fields_ = [
+        ("height", ctypes.c_int), ("width", ctypes.c_int),
+        ("sides", ctypes.POINTER(ctypes.c_int)), ("n_sides", ctypes.c_int),
+        ("alpha", ctypes.c_double), ("cmode", ctypes.c_int),
+        ("c_explicit", ctypes.POINTER(ctypes.c_double)),
+        ("max_cycles", ctypes.c_int), ("tol", ctypes.c_double), ("tol_relative", ctypes.c_int),
+        ("q_dtype", ctypes.c_int), ("icd_max_sweeps", ctypes.c_int),
+        ("maxstat_draws", ctypes.c_int), ("seed", ctypes.c_ulonglong), ("flags", ctypes.c_int),
+    ]
+
+
+class smre_result(ctypes.Structure):
+    _fields_ = [
+        ("cycles", ctypes.c_int), ("status", ctypes.c_int),
+        ("step", ctypes.c_double), ("rel_step", ctypes.c_double),
+        ("max_violation", ctypes.c_double), ("windows", ctypes.c_longlong),
+        ("max_tile_sweeps", ctypes.c_int), ("seconds", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+
+
+def lib_path() -> str:
+    return os.path.join(_PKG, "lib", "libsmre.so")
+
+
+_lib = None
+
+
+def load():
+    """Load libsmre.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = lib_path()
+    if not os.path.exists(p):
+        raise ImportError(f"{p} is missing: build it with `python -m paper_1503_03492_gb300.build`")
+    lib = ctypes.CDLL(p)
+    H = ctypes.c_void_p
+    P = ctypes.POINTER
+    st = ctypes.c_int
+    sig = {
+        "smre_bounds": (st, [P(smre_params), P(ctypes.c_double)]),
+        "smre_dykstra_create": (st, [P(smre_params), ctypes.c_void_p, P(H)]),
+        "smre_dykstra_project": (st, [H, ctypes.c_void_p, ctypes.c_void_p, P(smre_result)]),
+        "smre_dykstra_project_incomplete": (st, [H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                                 ctypes.c_double, P(smre_result)]),
+        "smre_dykstra_set_stopping": (st, [H, ctypes.c_int, ctypes.c_double, ctypes.c_int]),
+        "smre_dykstra_bounds": (st, [H, P(ctypes.c_int), P(ctypes.c_double), ctypes.c_int]),
+        "smre_dykstra_history": (st, [H, P(ctypes.c_double), ctypes.c_int, P(ctypes.c_int)]),
+        "smre_dykstra_icd_sweeps": (st, [H, P(ctypes.c_int), ctypes.c_int, P(ctypes.c_int)]),
+        "smre_dykstra_device_bytes": (ctypes.c_size_t, [H]),
+        "smre_dykstra_destroy": (None, [H]),
+        "smre_last_error": (ctypes.c_char_p, [H]),
+        "smre_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+# ------------------------------------------------------------ marshalling
+
+def _ptr(img):
+    """(address, keepalive) of a float32 C-contiguous H x W image."""
+    try:
+        import torch
+        if isinstance(img, torch.Tensor):
+            if img.dtype != torch.float32 or not img.is_contiguous() or img.dim() != 2:
+                raise ValueError("image must be a contiguous 2-D float32 tensor")
+            return img.data_ptr(), img
+    except ImportError:
+        pass
+    import numpy as np
+    if isinstance(img, np.ndarray):
+        if img.dtype != np.float32 or not img.flags.c_contiguous or img.ndim != 2:
+            raise ValueError("image must be a C-contiguous 2-D float32 array")
+        return img.ctypes.data, img
+    raise TypeError(f"unsupported image type {type(img)}")
+
+
+def _check(status, h=None, ok=(SMRE_OK,)):
+    if status not in ok:
+        msg = load().smre_last_error(h)
+        raise SmreError(status, msg.decode() if msg else "")
+    return status
+
+
+def make_params(H, W, sides, alpha=0.9, cmode=SMRE_C_PERSET, c_explicit=None, max_cycles=200,
+                tol=-1.0, tol_relative=False, icd_max_sweeps=0, maxstat_draws=0, seed=0, flags=0):
+    """Build an ``smre_params`` (the arrays it points to are kept on the object)."""
+    p = smre_params()
+    sides_arr = (ctypes.c_int * len(sides))(*[int(s) for s in sides])
+    p.height, p.width = int(H), int(W)
+    p.sides, p.n_sides = sides_arr, len(sides)
+    p.alpha, p.cmode = float(alpha), int(cmode)
+    if c_explicit is not None:
+        c_arr = (ctypes.c_double * len(c_explicit))(*[float(c) for c in c_explicit])
+        p.c_explicit = c_arr
+        p._c_keep = c_arr
+    p.max_cycles, p.tol, p.tol_relative = int(max_cycles), float(tol), int(bool(tol_relative))
+    p.q_dtype, p.icd_max_sweeps, p.maxstat_draws = 0, int(icd_max_sweeps), int(maxstat_draws)
+    p.seed, p.flags = int(seed), int(flags)
+    p._sides_keep = sides_arr
+    return p
+
+
+# ------------------------------------------------------- C-named functions
+
+def smre_version() -> str:
+    return load().smre_version().decode()
+
+
+def smre_last_error(h=None) -> str:
+    m = load().smre_last_error(h)
+    return m.decode() if m else ""
+
+
+def smre_bounds(params: smre_params):
+    out = (ctypes.c_double * params.n_sides)()
+    _check(load().smre_bounds(ctypes.byref(params), out))
+    return list(out)
+
+
+def smre_dykstra_create(params: smre_params, stream=None):
+    """Returns an opaque handle (int).  ``stream``: a cudaStream_t as int, a
+    ``torch.cuda.Stream``, or None for the legacy default stream."""
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    h = ctypes.c_void_p()
+    _check(load().smre_dykstra_create(ctypes.byref(params), ctypes.c_void_p(stream or 0),
+                                      ctypes.byref(h)))
+    return h.value
+
+
+def smre_dykstra_project(h, x0, x, want_result=True):
+    p0, k0 = _ptr(x0)
+    p1, k1 = _ptr(x)
+    res = smre_result()
+    st = load().smre_dykstra_project(h, p0, p1, ctypes.byref(res) if want_result else None)
+    _check(st, h, ok=(SMRE_OK, SMRE_ENOTCONVERGED))
+    return res if want_result else None
+
+
+def smre_dykstra_project_incomplete(h, x0, x, K=-1, tol=1e-3, want_result=True):
+    p0, k0 = _ptr(x0)
+    p1, k1 = _ptr(x)
+    res = smre_result()
+    st = load().smre_dykstra_project_incomplete(h, p0, p1, int(K), float(tol),
+                                                ctypes.byref(res) if want_result else None)
+    _check(st, h)
+    return res if want_result else None
+
+
+def smre_dykstra_set_stopping(h, max_cycles, tol, tol_relative=False):
+    _check(load().smre_dykstra_set_stopping(h, int(max_cycles), float(tol), int(bool(tol_relative))), h)
+
+
+def smre_dykstra_bounds(h, n=64):
+    s = (ctypes.c_int * n)()
+    c = (ctypes.c_double * n)()
+    _check(load().smre_dykstra_bounds(h, s, c, n), h)
+    out = {}
+    for i in range(n):
+        if s[i] <= 0:
+            break
+        out[s[i]] = c[i]
+    return out
+
+
+def smre_dykstra_history(h, n_max=1 << 20):
+    import numpy as np
+    n = ctypes.c_int()
+    _check(load().smre_dykstra_history(h, None, 0, ctypes.byref(n)), h)
+    buf = np.zeros((max(n.value, 1), 2))
+    _check(load().smre_dykstra_history(h, buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                       min(n.value, n_max), ctypes.byref(n)), h)
+    return buf[:n.value]
+
+
+def smre_dykstra_icd_sweeps(h):
+    import numpy as np
+    n = ctypes.c_int()
+    _check(load().smre_dykstra_icd_sweeps(h, None, 0, ctypes.byref(n)), h)
+    buf = np.zeros(max(n.value, 1), dtype=np.int32)
+    _check(load().smre_dykstra_icd_sweeps(h, buf.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                          n.value, ctypes.byref(n)), h)
+    return buf[:n.value]
+
+
+def smre_dykstra_device_bytes(h) -> int:
+    return int(load().smre_dykstra_device_bytes(h))
+
+
+def smre_dykstra_destroy(h):
+    load().smre_dykstra_destroy(h)
+
+
+class Projector:
+    """RAII wrapper: ``with Projector(H, W, sides, ...) as P: P.project(x0, x)``."""
+
+    def __init__(self, H, W, sides, stream=None, **kw):
+        self.params = make_params(H, W, sides, **kw)
+        self.h = smre_dykstra_create(self.params, stream)
+
+    def project(self, x0, x, want_result=True):
+        return smre_dykstra_project(self.h, x0, x, want_result)
+
+    def project_incomplete(self, x0, x, K=-1, tol=1e-3, want_result=True):
+        return smre_dykstra_project_incomplete(self.h, x0, x, K, tol, want_result)
+
+    def set_stopping(self, max_cycles, tol, tol_relative=False):
+        smre_dykstra_set_stopping(self.h, max_cycles, tol, tol_relative)
+
+    def bounds(self):
+        return smre_dykstra_bounds(self.h)
+
+    def history(self):
+        return smre_dykstra_history(self.h)
+
+    def icd_sweeps(self):
+        return smre_dykstra_icd_sweeps(self.h)
+
+    def device_bytes(self):
+        return smre_dykstra_device_bytes(self.h)
+
+    def close(self):
+        if self.h:
+            smre_dykstra_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

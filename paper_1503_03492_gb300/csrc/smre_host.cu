@@ -1,0 +1,625 @@
+// Host side of libsmre.so: argument checking, bounds, the cycle schedule
+// (Sec. 2.3 set order), device buffers and the C ABI of include/smre.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "smre_internal.h"
+
+using namespace smre;
+
+struct smre_dykstra {
+    // problem
+    int H = 0, W = 0, pitch = 0;
+    std::vector<int> sides;        // ascending, unique
+    std::vector<double> cS;        // aligned with sides
+    double cS_of[kMaxSide + 1] = {};
+    smre_cmode cmode = SMRE_C_PERSET;
+    double alpha = 0.9;
+    int maxstat_draws = 1000;
+    unsigned long long seed = 0;
+    int flags = 0;
+    // stopping rule
+    int max_cycles = 1;
+    double tol = -1.0;
+    int tol_relative = 0;
+    int icd_max_sweeps = 1000;
+    // schedule
+    std::vector<Group> groups;
+    std::vector<Tiling> tilings;
+    long long windows_per_cycle = 0;
+    // device state
+    cudaStream_t stream = nullptr;
+    float *q = nullptr;
+    size_t q_floats = 0;
+    float *xw = nullptr, *xprev = nullptr;
+    double *partials = nullptr;
+    int n_partials = 0;
+    double *hist = nullptr;
+    int hist_cap = 0;
+    Control *ctl = nullptr;
+    Control *ctl_host = nullptr;   // pinned
+    int *icd_sweeps = nullptr;
+    int icd_sweeps_cap = 0;
+    int last_icd_tiles = 0;
+    int last_cycles = 0;
+    double *viol = nullptr;
+    double *viol_host = nullptr;   // pinned
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    size_t dev_bytes = 0;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+smre_status fail(smre_dykstra *h, smre_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (h) h->err = buf; else g_err = buf;
+    return s;
+}
+
+#define CK(h, call)                                                                     \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return fail((h), e_ == cudaErrorMemoryAllocation ? SMRE_ENOMEM : SMRE_ECUDA, \
+                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+// Common validation of the problem description; fills sides (ascending).
+smre_status check_params(const smre_params *p, std::vector<int> &sides, std::vector<double> &cexp)
+{
+    if (!p) return fail(nullptr, SMRE_EINVAL, "params is NULL");
+    if (p->height < 1 || p->width < 1 || p->height > 65535)
+        return fail(nullptr, SMRE_EINVAL, "image %d x %d out of range", p->height, p->width);
+    if (p->width > kMaxWidth)
+        return fail(nullptr, SMRE_EINVAL, "width %d above the supported %d", p->width, kMaxWidth);
+    if (!p->sides || p->n_sides < 1 || p->n_sides > 64)
+        return fail(nullptr, SMRE_EINVAL, "need 1..64 window sides");
+    std::vector<std::pair<int, double>> sv;
+    for (int i = 0; i < p->n_sides; ++i) {
+        const int L = p->sides[i];
+        if (L < 1 || L > kMaxSide || L > p->height || L > p->width)
+            return fail(nullptr, SMRE_EINVAL, "window side %d outside 1..min(%d, H, W)", L, kMaxSide);
+        double c = 0.0;
+        if (p->cmode == SMRE_C_EXPLICIT) {
+            if (!p->c_explicit) return fail(nullptr, SMRE_EINVAL, "c_explicit is NULL");
+            c = p->c_explicit[i];
+            if (!(c > 0.0) || !std::isfinite(c))
+                return fail(nullptr, SMRE_EINVAL, "bound %g of side %d is not a positive number", c, L);
+        }
+        sv.emplace_back(L, c);
+    }
+    std::sort(sv.begin(), sv.end(), [](auto &a, auto &b) { return a.first < b.first; });
+    sides.clear();
+    cexp.clear();
+    for (auto &pr : sv)
+        if (sides.empty() || sides.back() != pr.first) {
+            sides.push_back(pr.first);
+            cexp.push_back(pr.second);
+        }
+    if (p->cmode != SMRE_C_EXPLICIT && !(p->alpha > 0.0 && p->alpha < 1.0))
+        return fail(nullptr, SMRE_EINVAL, "alpha %g outside (0, 1)", p->alpha);
+    if ((int)p->cmode < 0 || (int)p->cmode > 3)
+        return fail(nullptr, SMRE_EINVAL, "unknown cmode %d", (int)p->cmode);
+    if (p->q_dtype != 0) return fail(nullptr, SMRE_EINVAL, "q_dtype %d not supported", p->q_dtype);
+    if (p->max_cycles < 1) return fail(nullptr, SMRE_EINVAL, "max_cycles must be >= 1");
+    if (std::isnan(p->tol)) return fail(nullptr, SMRE_EINVAL, "tol is NaN");
+    if (p->icd_max_sweeps < 0 || p->maxstat_draws < 0)
+        return fail(nullptr, SMRE_EINVAL, "negative sweep cap or draw count");
+    return SMRE_OK;
+}
+
+// Monte Carlo quantile of Q_Omega on the device (MAXSTAT).
+smre_status maxstat_q(const smre_params *p, const std::vector<int> &sides, double &q_out)
+{
+    const int H = p->height, W = p->width, pitch = round_up(W, 32);
+    const int draws = p->maxstat_draws ? p->maxstat_draws : 1000;
+    const size_t per = (size_t)H * pitch;
+    int batch = (int)std::max<size_t>(1, std::min<size_t>(64, (size_t)(256u << 20) / (per * 4)));
+    batch = std::min(batch, draws);
+    float *img = nullptr;
+    double *mx = nullptr;
+    cudaStream_t s = nullptr;
+    std::vector<double> all(draws), part(batch);
+    cudaError_t e = cudaMalloc(&img, per * batch * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&mx, 2 * batch * sizeof(double));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    for (int d0 = 0; e == cudaSuccess && d0 < draws; d0 += batch) {
+        const int n = std::min(batch, draws - d0);
+        e = launch_maxstat(H, W, pitch, sides.data(), (int)sides.size(), d0, n, p->seed, img, mx, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(part.data(), mx + n, n * sizeof(double),
+                                                  cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        for (int i = 0; i < n && e == cudaSuccess; ++i) all[d0 + i] = part[i];
+    }
+    if (s) cudaStreamDestroy(s);
+    cudaFree(img);
+    cudaFree(mx);
+    if (e != cudaSuccess)
+        return fail(nullptr, e == cudaErrorMemoryAllocation ? SMRE_ENOMEM : SMRE_ECUDA,
+                    "MAXSTAT Monte Carlo: %s", cudaGetErrorString(e));
+    std::sort(all.begin(), all.end());
+    int idx = (int)std::ceil(p->alpha * draws) - 1;
+    idx = std::max(0, std::min(draws - 1, idx));
+    q_out = all[idx];
+    return SMRE_OK;
+}
+
+smre_status compute_bounds(const smre_params *p, const std::vector<int> &sides,
+                           const std::vector<double> &cexp, std::vector<double> &cS)
+{
+    cS.assign(sides.size(), 0.0);
+    switch (p->cmode) {
+        case SMRE_C_EXPLICIT: cS = cexp; return SMRE_OK;
+        case SMRE_C_CHI2:
+            for (size_t i = 0; i < sides.size(); ++i) cS[i] = chi2_quantile(p->alpha, sides[i] * sides[i]);
+            return SMRE_OK;
+        case SMRE_C_PERSET: {
+            const double q = inv_normal_cdf(p->alpha);
+            for (size_t i = 0; i < sides.size(); ++i) cS[i] = bound_from_q(q, sides[i]);
+            return SMRE_OK;
+        }
+        case SMRE_C_MAXSTAT: {
+            double q = 0.0;
+            smre_status st = maxstat_q(p, sides, q);
+            if (st != SMRE_OK) return st;
+            for (size_t i = 0; i < sides.size(); ++i) cS[i] = bound_from_q(q, sides[i]);
+            return SMRE_OK;
+        }
+    }
+    return fail(nullptr, SMRE_EINVAL, "unknown cmode");
+}
+
+// Set order of one cycle (Sec. 2.3): sides descending; per side L the groups
+// (L, a), a = 0..L-1, each holding the tilings (L, a, b), b = 0..L-1.
+void build_schedule(smre_dykstra *h)
+{
+    h->groups.clear();
+    h->tilings.clear();
+    long long off = 0;
+    h->windows_per_cycle = 0;
+    for (auto it = h->sides.rbegin(); it != h->sides.rend(); ++it) {
+        const int L = *it;
+        for (int a = 0; a < L; ++a) {
+            Group g;
+            g.L = L;
+            g.a = a;
+            g.n_units = (h->H - a) / L;
+            g.tiling0 = (int)h->tilings.size();
+            h->groups.push_back(g);
+            for (int b = 0; b < L; ++b) {
+                Tiling t;
+                t.L = L;
+                t.a = a;
+                t.b = b;
+                t.n_u = (h->H - a) / L;
+                t.n_v = (h->W - b) / L;
+                t.q_off = off;
+                off += (long long)t.n_u * L * h->pitch;
+                h->windows_per_cycle += (long long)t.n_u * t.n_v;
+                h->tilings.push_back(t);
+            }
+        }
+    }
+    h->q_floats = (size_t)off;
+}
+
+bool is_device_ptr(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+smre_status ensure_hist(smre_dykstra *h, int cap)
+{
+    if (cap <= h->hist_cap) return SMRE_OK;
+    if (h->hist) {
+        CK(h, cudaStreamSynchronize(h->stream));
+        cudaFree(h->hist);
+        h->dev_bytes -= sizeof(double) * 2 * h->hist_cap;
+        h->hist = nullptr;
+    }
+    CK(h, cudaMalloc(&h->hist, sizeof(double) * 2 * cap));
+    h->hist_cap = cap;
+    h->dev_bytes += sizeof(double) * 2 * cap;
+    return SMRE_OK;
+}
+
+smre_status stage_in(smre_dykstra *h, const float *x0)
+{
+    CK(h, cudaMemcpy2DAsync(h->xw, sizeof(float) * h->pitch, x0, sizeof(float) * h->W,
+                            sizeof(float) * h->W, h->H, cudaMemcpyDefault, h->stream));
+    return SMRE_OK;
+}
+
+smre_status stage_out(smre_dykstra *h, float *x)
+{
+    CK(h, cudaMemcpy2DAsync(x, sizeof(float) * h->W, h->xw, sizeof(float) * h->pitch,
+                            sizeof(float) * h->W, h->H, cudaMemcpyDefault, h->stream));
+    return SMRE_OK;
+}
+
+smre_status violation(smre_dykstra *h, double &out)
+{
+    ViolationArgs va{};
+    va.x = h->xw;
+    va.pitch = h->pitch;
+    va.H = h->H;
+    va.W = h->W;
+    va.n_sides = (int)h->sides.size();
+    for (int i = 0; i < va.n_sides; ++i) {
+        va.sides[i] = h->sides[i];
+        va.cS[i] = h->cS[i];
+    }
+    CK(h, launch_violation(va, h->partials, h->n_partials, h->viol, h->stream));
+    CK(h, cudaMemcpyAsync(h->viol_host, h->viol, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    out = *h->viol_host;
+    return SMRE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *smre_version(void) { return "smre-gb300 0.1 (sm_103a)"; }
+
+const char *smre_last_error(const smre_dykstra *h)
+{
+    if (h) return h->err.c_str();
+    return g_err.c_str();
+}
+
+smre_status smre_bounds(const smre_params *p, double *cS_out)
+{
+    std::vector<int> sides;
+    std::vector<double> cexp, cS;
+    smre_status st = check_params(p, sides, cexp);
+    if (st != SMRE_OK) return st;
+    if (!cS_out) return fail(nullptr, SMRE_EINVAL, "cS_out is NULL");
+    st = compute_bounds(p, sides, cexp, cS);
+    if (st != SMRE_OK) return st;
+    for (int i = 0; i < p->n_sides; ++i) {
+        const int L = p->sides[i];
+        const size_t j = std::lower_bound(sides.begin(), sides.end(), L) - sides.begin();
+        cS_out[i] = cS[j];
+    }
+    return SMRE_OK;
+}
+
+smre_status smre_dykstra_create(const smre_params *p, void *cuda_stream, smre_dykstra **out)
+{
+    if (!out) return fail(nullptr, SMRE_EINVAL, "out is NULL");
+    *out = nullptr;
+    std::vector<int> sides;
+    std::vector<double> cexp;
+    smre_status st = check_params(p, sides, cexp);
+    if (st != SMRE_OK) return st;
+    smre_dykstra *h = new (std::nothrow) smre_dykstra();
+    if (!h) return fail(nullptr, SMRE_ENOMEM, "host allocation failed");
+    h->H = p->height;
+    h->W = p->width;
+    h->pitch = round_up(p->width, 32);
+    h->sides = sides;
+    h->cmode = p->cmode;
+    h->alpha = p->alpha;
+    h->maxstat_draws = p->maxstat_draws ? p->maxstat_draws : 1000;
+    h->seed = p->seed;
+    h->flags = p->flags;
+    h->max_cycles = p->max_cycles;
+    h->tol = p->tol;
+    h->tol_relative = p->tol_relative ? 1 : 0;
+    h->icd_max_sweeps = p->icd_max_sweeps ? p->icd_max_sweeps : 1000;
+    h->stream = (cudaStream_t)cuda_stream;
+
+    st = compute_bounds(p, sides, cexp, h->cS);
+    if (st != SMRE_OK) {
+        delete h;
+        return st;
+    }
+    for (size_t i = 0; i < sides.size(); ++i) h->cS_of[sides[i]] = h->cS[i];
+    build_schedule(h);
+
+    auto bail = [&](smre_status s2) {
+        g_err = h->err;
+        smre_dykstra_destroy(h);
+        return s2;
+    };
+#define CKC(call)                                                                         \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess) {                                                          \
+            fail(h, e_ == cudaErrorMemoryAllocation ? SMRE_ENOMEM : SMRE_ECUDA, "%s: %s", \
+                 #call, cudaGetErrorString(e_));                                          \
+            return bail(e_ == cudaErrorMemoryAllocation ? SMRE_ENOMEM : SMRE_ECUDA);     \
+        }                                                                                 \
+    } while (0)
+
+    const size_t img = sizeof(float) * (size_t)h->H * h->pitch;
+    CKC(cudaMalloc(&h->q, sizeof(float) * std::max<size_t>(h->q_floats, 1)));
+    CKC(cudaMalloc(&h->xw, img));
+    CKC(cudaMalloc(&h->xprev, img));
+    CKC(cudaMemset(h->xw, 0, img));
+    CKC(cudaMemset(h->xprev, 0, img));
+    h->n_partials = norm_blocks();
+    CKC(cudaMalloc(&h->partials, sizeof(double) * 2 * h->n_partials));
+    CKC(cudaMalloc(&h->ctl, sizeof(Control)));
+    CKC(cudaMalloc(&h->viol, sizeof(double)));
+    CKC(cudaMallocHost(&h->ctl_host, sizeof(Control)));
+    CKC(cudaMallocHost(&h->viol_host, sizeof(double)));
+    CKC(cudaEventCreate(&h->ev0));
+    CKC(cudaEventCreate(&h->ev1));
+    h->dev_bytes = sizeof(float) * std::max<size_t>(h->q_floats, 1) + 2 * img +
+                   sizeof(double) * 2 * h->n_partials + sizeof(Control) + sizeof(double);
+    if (ensure_hist(h, h->max_cycles) != SMRE_OK) return bail(SMRE_ENOMEM);
+#undef CKC
+    *out = h;
+    return SMRE_OK;
+}
+
+smre_status smre_dykstra_set_stopping(smre_dykstra *h, int max_cycles, double tol, int tol_relative)
+{
+    if (!h) return fail(nullptr, SMRE_EINVAL, "handle is NULL");
+    if (max_cycles < 1) return fail(h, SMRE_EINVAL, "max_cycles must be >= 1");
+    if (std::isnan(tol)) return fail(h, SMRE_EINVAL, "tol is NaN");
+    smre_status st = ensure_hist(h, max_cycles);
+    if (st != SMRE_OK) return st;
+    h->max_cycles = max_cycles;
+    h->tol = tol;
+    h->tol_relative = tol_relative ? 1 : 0;
+    return SMRE_OK;
+}
+
+smre_status smre_dykstra_project(smre_dykstra *h, const float *x0, float *x, smre_result *res)
+{
+    if (!h) return fail(nullptr, SMRE_EINVAL, "handle is NULL");
+    if (!x0 || !x) return fail(h, SMRE_EINVAL, "x0 / x is NULL");
+    smre_status st = stage_in(h, x0);
+    if (st != SMRE_OK) return st;
+    CK(h, cudaMemcpy2DAsync(h->xprev, sizeof(float) * h->pitch, h->xw, sizeof(float) * h->pitch,
+                            sizeof(float) * h->W, h->H, cudaMemcpyDeviceToDevice, h->stream));
+    CK(h, cudaMemsetAsync(h->ctl, 0, sizeof(Control), h->stream));
+    CK(h, cudaEventRecord(h->ev0, h->stream));
+
+    int cycles = 0;
+    for (int cyc = 0; cyc < h->max_cycles; ++cyc) {
+        for (const Group &g : h->groups) {
+            GroupArgs A{};
+            A.x = h->xw;
+            A.q = h->q;
+            for (int b = 0; b < g.L; ++b) A.q_off[b] = h->tilings[g.tiling0 + b].q_off;
+            A.pitch = h->pitch;
+            A.H = h->H;
+            A.W = h->W;
+            A.L = g.L;
+            A.a = g.a;
+            A.n_units = g.n_units;
+            A.cS = (float)h->cS_of[g.L];
+            A.cS64 = h->cS_of[g.L];
+            A.first = cyc == 0;
+            CK(h, launch_group(A, h->stream));
+        }
+        CK(h, launch_cycle_norm(h->xw, h->xprev, h->H, h->W, h->pitch, h->partials,
+                                h->n_partials, h->stream));
+        CK(h, launch_decide(h->partials, h->n_partials, h->ctl, h->hist, h->hist_cap, h->tol,
+                            h->tol_relative, h->stream));
+        CK(h, cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(Control), cudaMemcpyDeviceToHost,
+                              h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+        cycles = cyc + 1;
+        if (h->ctl_host->stop) break;
+    }
+    CK(h, cudaEventRecord(h->ev1, h->stream));
+    h->last_cycles = cycles;
+    double viol = NAN;
+    if (h->flags & SMRE_F_VIOLATION) {
+        st = violation(h, viol);
+        if (st != SMRE_OK) return st;
+    }
+    st = stage_out(h, x);
+    if (st != SMRE_OK) return st;
+    if (res) {
+        CK(h, cudaStreamSynchronize(h->stream));
+        float ms = 0.f;
+        CK(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+        res->cycles = h->ctl_host->cycles;
+        res->status = h->ctl_host->status;
+        res->step = h->ctl_host->step;
+        res->rel_step = h->ctl_host->prev_norm > 0 ? h->ctl_host->step / h->ctl_host->prev_norm : 0.0;
+        res->max_violation = viol;
+        res->windows = (long long)res->cycles * h->windows_per_cycle;
+        res->max_tile_sweeps = 0;
+        res->seconds = ms * 1e-3;
+        return (smre_status)res->status;
+    }
+    return SMRE_OK;
+}
+
+smre_status smre_dykstra_project_incomplete(smre_dykstra *h, const float *x0, float *x, int K,
+                                            double tol, smre_result *res)
+{
+    if (!h) return fail(nullptr, SMRE_EINVAL, "handle is NULL");
+    if (!x0 || !x) return fail(h, SMRE_EINVAL, "x0 / x is NULL");
+    if (K < 0) K = (int)std::floor(std::log2((double)h->sides.back()) + 1e-12);
+    if (K > kMaxIcdK) return fail(h, SMRE_EINVAL, "K = %d above the supported %d", K, kMaxIcdK);
+    const int B = 1 << K;
+    if (B > h->H || B > h->W) return fail(h, SMRE_EINVAL, "tile side %d larger than the image", B);
+    if (std::isnan(tol)) return fail(h, SMRE_EINVAL, "tol is NaN");
+    float cS[kMaxIcdK + 1];
+    double cS64[kMaxIcdK + 1];
+    for (int k = 0; k <= K; ++k) {
+        const int L = 1 << k;
+        double c = 0.0;
+        if (L <= kMaxSide && h->cS_of[L] > 0.0) c = h->cS_of[L];
+        else if (h->cmode == SMRE_C_PERSET) c = bound_from_q(inv_normal_cdf(h->alpha), L);
+        else if (h->cmode == SMRE_C_CHI2) c = chi2_quantile(h->alpha, L * L);
+        else
+            return fail(h, SMRE_EINVAL, "no bound for side %d: add it to the sides", L);
+        cS[k] = (float)c;
+        cS64[k] = c;
+    }
+    // tile counts of every pass
+    std::vector<int> ni(K + 1), nj(K + 1), offs(K + 1);
+    int total = 0;
+    for (int i = 0; i <= K; ++i) {
+        offs[i] = (1 << i) % B;
+        ni[i] = h->H - offs[i] >= B ? (h->H - offs[i]) / B : 0;
+        nj[i] = h->W - offs[i] >= B ? (h->W - offs[i]) / B : 0;
+        total += ni[i] * nj[i];
+    }
+    if (total > h->icd_sweeps_cap) {
+        if (h->icd_sweeps) {
+            CK(h, cudaStreamSynchronize(h->stream));
+            cudaFree(h->icd_sweeps);
+            h->dev_bytes -= sizeof(int) * h->icd_sweeps_cap;
+            h->icd_sweeps = nullptr;
+        }
+        CK(h, cudaMalloc(&h->icd_sweeps, sizeof(int) * std::max(total, 1)));
+        h->icd_sweeps_cap = std::max(total, 1);
+        h->dev_bytes += sizeof(int) * h->icd_sweeps_cap;
+    }
+    smre_status st = stage_in(h, x0);
+    if (st != SMRE_OK) return st;
+    CK(h, cudaEventRecord(h->ev0, h->stream));
+    int o = 0;
+    for (int i = 0; i <= K; ++i) {
+        IcdArgs A{};
+        A.x = h->xw;
+        A.pitch = h->pitch;
+        A.H = h->H;
+        A.W = h->W;
+        A.K = K;
+        A.pass = i;
+        A.off = offs[i];
+        A.n_ti = ni[i];
+        A.n_tj = nj[i];
+        A.tol_b2 = (float)(tol * (double)B * (double)B);
+        A.max_sweeps = h->icd_max_sweeps;
+        for (int k = 0; k <= K; ++k) {
+            A.cS[k] = cS[k];
+            A.cS64[k] = cS64[k];
+        }
+        A.sweeps = h->icd_sweeps + o;
+        CK(h, launch_icd_pass(A, h->stream));
+        o += ni[i] * nj[i];
+    }
+    CK(h, cudaEventRecord(h->ev1, h->stream));
+    h->last_icd_tiles = total;
+    double viol = NAN;
+    if (h->flags & SMRE_F_VIOLATION) {
+        st = violation(h, viol);
+        if (st != SMRE_OK) return st;
+    }
+    st = stage_out(h, x);
+    if (st != SMRE_OK) return st;
+    if (res) {
+        std::vector<int> sw(std::max(total, 1));
+        CK(h, cudaMemcpyAsync(sw.data(), h->icd_sweeps, sizeof(int) * total,
+                              cudaMemcpyDeviceToHost, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+        float ms = 0.f;
+        CK(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+        long long windows = 0, sweeps = 0;
+        int mx = 0;
+        o = 0;
+        for (int i = 0; i <= K; ++i) {
+            long long per_sweep = 0;
+            for (int k = i; k <= K; ++k) per_sweep += (long long)(B >> k) * (B >> k);
+            for (int t = 0; t < ni[i] * nj[i]; ++t) {
+                windows += per_sweep * sw[o + t];
+                sweeps += sw[o + t];
+                mx = std::max(mx, sw[o + t]);
+            }
+            o += ni[i] * nj[i];
+        }
+        res->cycles = (int)std::min<long long>(sweeps, 2147483647LL);
+        res->status = SMRE_OK;
+        res->step = NAN;
+        res->rel_step = NAN;
+        res->max_violation = viol;
+        res->windows = windows;
+        res->max_tile_sweeps = mx;
+        res->seconds = ms * 1e-3;
+    }
+    return SMRE_OK;
+}
+
+smre_status smre_dykstra_bounds(const smre_dykstra *h, int *sides_out, double *cS_out, int n)
+{
+    if (!h) return fail(nullptr, SMRE_EINVAL, "handle is NULL");
+    if (n < (int)h->sides.size() || !sides_out || !cS_out)
+        return fail(const_cast<smre_dykstra *>(h), SMRE_EINVAL, "need room for %zu sides",
+                    h->sides.size());
+    for (size_t i = 0; i < h->sides.size(); ++i) {
+        sides_out[i] = h->sides[i];
+        cS_out[i] = h->cS[i];
+    }
+    return SMRE_OK;
+}
+
+smre_status smre_dykstra_history(smre_dykstra *h, double *out, int n_max, int *n_cycles)
+{
+    if (!h) return fail(nullptr, SMRE_EINVAL, "handle is NULL");
+    CK(h, cudaStreamSynchronize(h->stream));
+    const int n = std::min(h->last_cycles, h->hist_cap);
+    if (n_cycles) *n_cycles = n;
+    const int m = std::min(n, std::max(n_max, 0));
+    if (m > 0 && out)
+        CK(h, cudaMemcpy(out, h->hist, sizeof(double) * 2 * m, cudaMemcpyDeviceToHost));
+    return SMRE_OK;
+}
+
+smre_status smre_dykstra_icd_sweeps(smre_dykstra *h, int *out, int n_max, int *n_tiles)
+{
+    if (!h) return fail(nullptr, SMRE_EINVAL, "handle is NULL");
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (n_tiles) *n_tiles = h->last_icd_tiles;
+    const int m = std::min(h->last_icd_tiles, std::max(n_max, 0));
+    if (m > 0 && out)
+        CK(h, cudaMemcpy(out, h->icd_sweeps, sizeof(int) * m, cudaMemcpyDeviceToHost));
+    return SMRE_OK;
+}
+
+size_t smre_dykstra_device_bytes(const smre_dykstra *h) { return h ? h->dev_bytes : 0; }
+
+void smre_dykstra_destroy(smre_dykstra *h)
+{
+    if (!h) return;
+    if (h->stream || h->q) cudaStreamSynchronize(h->stream);
+    cudaFree(h->q);
+    cudaFree(h->xw);
+    cudaFree(h->xprev);
+    cudaFree(h->partials);
+    cudaFree(h->hist);
+    cudaFree(h->ctl);
+    cudaFree(h->icd_sweeps);
+    cudaFree(h->viol);
+    if (h->ctl_host) cudaFreeHost(h->ctl_host);
+    if (h->viol_host) cudaFreeHost(h->viol_host);
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
+    delete h;
+}
+
+}  // extern "C"

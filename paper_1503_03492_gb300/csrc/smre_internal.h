@@ -1,0 +1,100 @@
+// Internal declarations shared by the translation units of libsmre.so.
+// Nothing here is part of the public C ABI (include/smre.h).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "smre.h"
+
+namespace smre {
+
+constexpr int kMaxSide = 32;      // largest window side the kernels are built for
+constexpr int kMaxWidth = 4096;   // widest image (one CTA holds a full window-row)
+constexpr int kMaxIcdK = 5;       // incomplete Dykstra: B = 2^K <= 32
+
+// Device-side control block of one projection (lives in device memory).
+struct Control {
+    int stop;        // 1 once the stopping test held (or the cap was reached)
+    int cycles;      // cycles completed
+    int status;      // smre_status seen on the device
+    int pad;
+    double step;     // |x_r - x_{r-1}|_2 of the last completed cycle
+    double prev_norm;
+};
+
+// One group (L, a): the L tilings (L, a, b), b = 0..L-1, share the same
+// window-rows ("units": rows a + L u .. a + L u + L - 1, u < n_units), so one
+// CTA can run all L passes of a unit back to back with block-local barriers.
+struct Group {
+    int L, a, n_units;
+    int tiling0;          // index of tiling (L, a, 0) in the cycle order
+};
+
+// Tiling (L, a, b): windows with top-left (a + L u, b + L v) fully inside.
+// Its increments live in n_u blocks of L rows x qpitch floats; block u starts
+// at q_off + u * L * qpitch, column j of a row holds pixel column b + j.
+struct Tiling {
+    int L, a, b, n_u, n_v;
+    long long q_off;      // in floats
+};
+
+// Arguments of one launch of the group kernel.
+struct GroupArgs {
+    float *x;             // work image, H x pitch
+    float *q;             // increment store
+    long long q_off[kMaxSide];  // q_off of tiling (L, a, b) for b = 0..L-1
+    int pitch, H, W;
+    int L, a, n_units;
+    float cS;             // bound of side L (FP32 copy for the fast test)
+    double cS64;          // the same bound in FP64 for the near-boundary recheck
+    int first;            // 1: first cycle, stored increments are taken as 0
+};
+
+// Launchers (defined next to their kernels).
+cudaError_t launch_group(const GroupArgs &args, cudaStream_t s);
+cudaError_t launch_cycle_norm(const float *x, float *xprev, int H, int W, int pitch,
+                              double *partials, int n_blocks, cudaStream_t s);
+cudaError_t launch_decide(const double *partials, int n_blocks, Control *ctl, double *hist,
+                          int max_cycles, double tol, int tol_relative, cudaStream_t s);
+int norm_blocks();
+
+struct ViolationArgs {
+    const float *x;
+    int pitch, H, W;
+    int n_sides;
+    int sides[kMaxSide];
+    double cS[kMaxSide];
+};
+cudaError_t launch_violation(const ViolationArgs &a, double *partials, int n_blocks,
+                             double *out, cudaStream_t s);
+
+struct IcdArgs {
+    float *x;             // work image, H x pitch
+    int pitch, H, W;
+    int K, pass, off;     // level count K, pass i, offset (1 << i) mod B
+    int n_ti, n_tj;       // tiles of this pass
+    float tol_b2;         // tol * B^2
+    int max_sweeps;
+    float cS[kMaxIcdK + 1];      // bound of side 2^k
+    double cS64[kMaxIcdK + 1];
+    int *sweeps;          // per-tile sweep counts of this pass (n_ti * n_tj)
+};
+cudaError_t launch_icd_pass(const IcdArgs &a, cudaStream_t s);
+
+// Host FP64 helpers of Sec. 2.1 (smre_weights.cu).
+double inv_normal_cdf(double p);
+double chi2_quantile(double alpha, int k);
+double bound_from_q(double q, int L);
+
+// Monte Carlo of Q_Omega (Sec. 2.1) for the MAXSTAT bounds: per-draw maxima of
+// draws draw0 .. draw0 + n_draws - 1 land in maxima[n_draws .. 2 n_draws);
+// img holds n_draws * H * pitch floats, maxima 2 * n_draws doubles.
+cudaError_t launch_maxstat(int H, int W, int pitch, const int *sides, int n_sides, int draw0,
+                           int n_draws, unsigned long long seed, float *img, double *maxima,
+                           cudaStream_t s);
+
+}  // namespace smre

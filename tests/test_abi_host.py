@@ -1,0 +1,97 @@
+"""Host-side checks of libsmre.so that need no GPU: the library loads, exports
+every entry point include/smre.h declares, computes the Sec. 2.1 bounds on
+the host like the oracle does, and rejects bad arguments before touching CUDA.
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def smre():
+    from paper_1503_03492_gb300 import build as b
+    b.build()
+    import paper_1503_03492_gb300 as m
+    return m
+
+
+def _declared():
+    names = []
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            names += re.findall(r"SMRE_API[^;(]*?\b(smre_\w+)\s*\(", txt)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol(smre):
+    declared = _declared()
+    assert "smre_dykstra_create" in declared and "smre_dykstra_project_incomplete" in declared
+    lib = ctypes.CDLL(smre.lib_path())
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert sorted(smre.EXPORTED) == declared
+
+
+def test_version(smre):
+    assert "sm_103a" in smre.smre_version()
+
+
+@pytest.mark.parametrize("mode,omode", [(0, "perset"), (1, "chi2")])
+def test_host_bounds_match_oracle(smre, oracle_mod, mode, omode):
+    sides = list(range(1, 17))
+    for alpha in (0.5, 0.9, 0.99):
+        p = smre.make_params(64, 64, sides, alpha=alpha, cmode=mode)
+        got = np.array(smre.smre_bounds(p))
+        ref = oracle_mod.bounds(sides, alpha, omode)
+        assert np.allclose(got, ref, rtol=1e-12, atol=0), (alpha, got - ref)
+
+
+def test_host_bounds_explicit_and_order(smre):
+    p = smre.make_params(32, 32, [4, 1, 2], cmode=smre.SMRE_C_EXPLICIT, c_explicit=[5.0, 1.5, 3.0])
+    assert smre.smre_bounds(p) == [5.0, 1.5, 3.0]
+
+
+@pytest.mark.parametrize("kw,msg", [
+    (dict(H=0, W=8, sides=[1]), "out of range"),
+    (dict(H=8, W=5000, sides=[1]), "width"),
+    (dict(H=8, W=8, sides=[9]), "window side"),
+    (dict(H=40, W=40, sides=[33]), "window side"),
+    (dict(H=8, W=8, sides=[0]), "window side"),
+    (dict(H=8, W=8, sides=[1], alpha=1.0), "alpha"),
+    (dict(H=8, W=8, sides=[1], max_cycles=0), "max_cycles"),
+    (dict(H=8, W=8, sides=[1], tol=float("nan")), "NaN"),
+    (dict(H=8, W=8, sides=[1, 2], cmode=3, c_explicit=[1.0, -2.0]), "positive"),
+])
+def test_create_rejects_bad_arguments_without_cuda(smre, kw, msg):
+    H, W, sides = kw.pop("H"), kw.pop("W"), kw.pop("sides")
+    p = smre.make_params(H, W, sides, **kw)
+    with pytest.raises(smre.SmreError) as ei:
+        smre.smre_dykstra_create(p)
+    assert ei.value.status == smre.SMRE_EINVAL
+    assert msg in str(ei.value)
+
+
+def test_null_handle_calls_fail_cleanly(smre):
+    lib = smre.load()
+    assert lib.smre_dykstra_project(None, None, None, None) == smre.SMRE_EINVAL
+    assert lib.smre_dykstra_set_stopping(None, 1, 0.0, 0) == smre.SMRE_EINVAL
+    assert lib.smre_dykstra_device_bytes(None) == 0
+    lib.smre_dykstra_destroy(None)
+    assert b"NULL" in lib.smre_last_error(None)
+
+
+def test_product_package_does_not_reach_the_oracle():
+    """The product package neither imports nor links the oracle."""
+    pkg = os.path.join(ROOT, "paper_1503_03492_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for fn in files:
+            if fn.endswith((".py", ".cu", ".h", ".cpp")):
+                txt = open(os.path.join(dirpath, fn)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt, fn
+                assert "smre_oracle" not in txt and "liboracle" not in txt, fn

@@ -1,0 +1,251 @@
+"""Parity of the sm_103a path (through the C ABI) with the FP64 oracle.
+
+Error metric (max-abs relative): err = max|x_gpu - x_ref| / max|x_ref|; the
+bar for FP32 is err <= 1e-5.  Both sides start from the same FP32-rounded
+input and use the same explicit bounds.
+"""
+import os
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+NTH = os.cpu_count() or 1
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    return torch
+
+
+@pytest.fixture(scope="module")
+def smre(torch_cuda):
+    import paper_1503_03492_gb300 as m
+    return m
+
+
+def err(a, ref):
+    return float(np.abs(np.asarray(a, np.float64) - ref).max() / max(np.abs(ref).max(), 1e-300))
+
+
+def run_std(smre, torch, x0, sides, cS, max_cycles, tol=-1.0, rel=False, flags=0, stream=None):
+    H, W = x0.shape
+    with smre.Projector(H, W, sides, stream=stream, cmode=smre.SMRE_C_EXPLICIT,
+                        c_explicit=list(cS), max_cycles=max_cycles, tol=tol, tol_relative=rel,
+                        flags=flags) as P:
+        xd = torch.from_numpy(np.ascontiguousarray(x0, np.float32)).cuda()
+        out = torch.empty_like(xd)
+        res = P.project(xd, out)
+        hist = P.history()
+        return out.cpu().numpy(), res, hist
+
+
+def f32(x):
+    return np.ascontiguousarray(x, np.float32)
+
+
+# ------------------------------------------------------------ one cycle
+
+@pytest.mark.parametrize("H,W,sides", [
+    (64, 64, [1, 2, 4]),
+    (37, 53, [1, 2, 3, 5]),          # ragged: no side divides the extents
+    (16, 16, [16]),                   # single window, maximum side
+    (19, 300, [7, 8, 9]),            # wide, sides larger than a warp share
+    (70, 33, list(range(1, 9))),
+    (5, 1029, [1, 2, 3, 4, 5]),      # two columns per thread, ragged tail
+    (9, 2500, [2, 9]),               # four columns per thread
+])
+def test_one_and_three_cycles_match_oracle(smre, torch_cuda, oracle_mod, H, W, sides):
+    from synthetic import blobs_residual
+    x0 = f32(blobs_residual(H, W, n_blobs=max(1, H * W // 800), seed=H * 1000 + W))
+    cS = oracle_mod.bounds(sides, 0.9)
+    for cyc in (1, 3):
+        got, res, hist = run_std(smre, torch_cuda, x0, sides, cS, cyc)
+        ref = oracle_mod.dykstra(x0.astype(np.float64), sides, cS, max_cycles=cyc, tol=-1,
+                                 n_threads=NTH)
+        assert res.cycles == cyc
+        assert err(got, ref.x) <= TOL, err(got, ref.x)
+        assert np.allclose(hist, ref.hist, rtol=1e-4, atol=1e-6 * np.abs(ref.hist).max())
+
+
+def test_window_count_reported(smre, torch_cuda, oracle_mod):
+    x0 = f32(np.random.default_rng(0).standard_normal((33, 47)) * 3)
+    sides = [1, 3, 4]
+    _, res, _ = run_std(smre, torch_cuda, x0, sides, oracle_mod.bounds(sides, 0.9), 2)
+    assert res.windows == 2 * oracle_mod.n_windows(33, 47, sides)
+
+
+# ------------------------------------------------------- closed forms
+
+def test_feasible_input_is_identity(smre, torch_cuda, oracle_mod):
+    sides = [1, 2, 3, 4]
+    x0 = f32(np.random.default_rng(1).standard_normal((40, 36)) * 0.1)
+    got, res, _ = run_std(smre, torch_cuda, x0, sides, oracle_mod.bounds(sides, 0.9), 50, tol=0.0)
+    assert res.cycles == 1 and res.step == 0.0
+    assert np.array_equal(got, x0)
+
+
+def test_disjoint_sets_elementwise(smre, torch_cuda):
+    x0 = f32(np.random.default_rng(2).standard_normal((31, 45)) * 3)
+    got, _, _ = run_std(smre, torch_cuda, x0, [1], [2.0], 2)
+    ref = x0.astype(np.float64) * np.minimum(1.0, np.sqrt(2.0) / np.abs(x0.astype(np.float64)))
+    assert err(got, ref) <= 2e-7
+
+
+def test_single_ball(smre, torch_cuda):
+    for L in (3, 8, 13):
+        x0 = f32(np.random.default_rng(L).standard_normal((L, L)) * 3)
+        c = 0.3 * float((x0.astype(np.float64) ** 2).sum())
+        got, _, _ = run_std(smre, torch_cuda, x0, [L], [c], 2)
+        ref = x0 * np.sqrt(c / (x0.astype(np.float64) ** 2).sum())
+        assert err(got, ref) <= 2e-7
+
+
+# --------------------------------------------------- full workloads
+
+def test_blobs_64_200_cycles(smre, torch_cuda, oracle_mod):
+    """64 x 64 blobs, sides {1,2,4}, alpha 0.9, 200 cycles or step < 1e-10."""
+    from synthetic import blobs_residual
+    sides = [1, 2, 4]
+    x0 = f32(blobs_residual())
+    cS = oracle_mod.bounds(sides, 0.9)
+    got, res, hist = run_std(smre, torch_cuda, x0, sides, cS, 200, tol=1e-10)
+    ref = oracle_mod.dykstra(x0.astype(np.float64), sides, cS, max_cycles=200, tol=1e-10)
+    assert res.cycles == ref.cycles == 200
+    assert res.status == smre.SMRE_ENOTCONVERGED
+    assert err(got, ref.x) <= TOL, err(got, ref.x)
+
+
+@pytest.fixture(scope="module")
+def emitter512(oracle_mod):
+    from synthetic import emitter_residual
+    x0 = f32(emitter_residual())
+    sides = list(range(1, 9))
+    return x0, sides, oracle_mod.bounds(sides, 0.9)
+
+
+def test_emitters_512_to_convergence(smre, torch_cuda, oracle_mod, emitter512):
+    """512 x 512 emitters, sides 1..8, relative step < 1e-6: the workload the
+    benchmark times, in the same configuration."""
+    x0, sides, cS = emitter512
+    got, res, hist = run_std(smre, torch_cuda, x0, sides, cS, 5000, tol=1e-6, rel=True,
+                             flags=smre.SMRE_F_VIOLATION)
+    assert res.status == smre.SMRE_OK
+    ref = oracle_mod.dykstra(x0.astype(np.float64), sides, cS, max_cycles=res.cycles, tol=-1,
+                             n_threads=NTH)
+    e = err(got, ref.x)
+    assert e <= TOL, e
+    # the oracle's own stopping cycle is within a few cycles of the device's
+    full = ref.hist[:, 0] / ref.hist[:, 1]
+    assert full[-1] <= 1.05e-6
+    assert abs(res.max_violation - oracle_mod.max_violation(ref.x, sides, cS)) < 1e-4
+
+
+def test_determinism_and_host_pointers(smre, torch_cuda, oracle_mod):
+    from synthetic import emitter_residual
+    x0 = f32(emitter_residual(96, 128, n_emitters=20, seed=5))
+    sides = [1, 2, 3, 5]
+    cS = oracle_mod.bounds(sides, 0.9)
+    a, _, _ = run_std(smre, torch_cuda, x0, sides, cS, 7)
+    b, _, _ = run_std(smre, torch_cuda, x0, sides, cS, 7)
+    assert np.array_equal(a, b)
+    with smre.Projector(96, 128, sides, cmode=3, c_explicit=list(cS), max_cycles=7) as P:
+        out = np.empty_like(x0)
+        P.project(x0, out)                      # host in, host out
+        assert np.array_equal(out, a)
+        xd = torch_cuda.from_numpy(x0.copy()).cuda()
+        P.project(xd, xd)                       # in place on the device
+        assert np.array_equal(xd.cpu().numpy(), a)
+
+
+def test_non_default_stream(smre, torch_cuda, oracle_mod):
+    x0 = f32(np.random.default_rng(3).standard_normal((64, 96)) * 3)
+    sides = [2, 3]
+    cS = oracle_mod.bounds(sides, 0.9)
+    s = torch_cuda.cuda.Stream()
+    got, res, _ = run_std(smre, torch_cuda, x0, sides, cS, 4, stream=s)
+    ref = oracle_mod.dykstra(x0.astype(np.float64), sides, cS, max_cycles=4, tol=-1)
+    assert err(got, ref.x) <= TOL
+
+
+# ------------------------------------------------- incomplete Dykstra
+
+def run_icd(smre, torch, x0, sides, cS, K, tol, max_sweeps=1000):
+    H, W = x0.shape
+    with smre.Projector(H, W, sides, cmode=smre.SMRE_C_EXPLICIT, c_explicit=list(cS),
+                        max_cycles=1, icd_max_sweeps=max_sweeps) as P:
+        xd = torch.from_numpy(x0).cuda()
+        out = torch.empty_like(xd)
+        res = P.project_incomplete(xd, out, K=K, tol=tol)
+        return out.cpu().numpy(), res, P.icd_sweeps()
+
+
+@pytest.mark.parametrize("H,W,K", [(64, 64, 0), (45, 50, 1), (64, 72, 2), (77, 91, 3),
+                                   (96, 100, 4), (100, 130, 5)])
+def test_icd_fixed_sweeps_matches_oracle(smre, torch_cuda, oracle_mod, H, W, K):
+    """tol < 0: every tile runs exactly max_sweeps sweeps on both sides, so the
+    comparison does not depend on a floating-point stopping decision."""
+    from synthetic import blobs_residual
+    x0 = f32(blobs_residual(H, W, n_blobs=4, seed=K + 40))
+    sides = [1 << k for k in range(K + 1)]
+    cS = oracle_mod.bounds(sides, 0.9)
+    for sweeps in (1, 6):
+        got, res, sw = run_icd(smre, torch_cuda, x0, sides, cS, K, -1.0, sweeps)
+        ref = oracle_mod.icd(x0.astype(np.float64), K, cS, tol=-1.0, max_sweeps=sweeps)
+        ref_sw = np.concatenate([s.ravel() for s in ref.sweeps])
+        assert np.array_equal(sw, ref_sw)
+        assert err(got, ref.x) <= TOL, (sweeps, err(got, ref.x))
+
+
+def test_icd_paper_tolerance_512(smre, torch_cuda, oracle_mod, emitter512):
+    """512 x 512 emitters, K = 3 (sides 1, 2, 4, 8), the paper's tol 1e-3.
+    Tiles whose sweep count agrees must agree in value; disagreements can only
+    come from an L1 change within FP32 rounding of tol * B^2."""
+    x0, _, _ = emitter512
+    sides = [1, 2, 4, 8]
+    cS = oracle_mod.bounds(sides, 0.9)
+    got, res, sw = run_icd(smre, torch_cuda, x0, sides, cS, 3, 1e-3)
+    ref = oracle_mod.icd(x0.astype(np.float64), 3, cS, tol=1e-3)
+    ref_sw = np.concatenate([s.ravel() for s in ref.sweeps])
+    agree = (sw == ref_sw).mean()
+    assert agree >= 0.99, agree
+    if agree == 1.0:
+        assert err(got, ref.x) <= TOL, err(got, ref.x)
+    assert res.windows > 0 and res.max_tile_sweeps == sw.max()
+
+
+def test_icd_tight_tolerance(smre, torch_cuda, oracle_mod):
+    from synthetic import emitter_residual
+    x0 = f32(emitter_residual(128, 128, n_emitters=40, seed=8))
+    sides = [1, 2, 4, 8]
+    cS = oracle_mod.bounds(sides, 0.9)
+    got, _, _ = run_icd(smre, torch_cuda, x0, sides, cS, 3, 1e-9, 3000)
+    ref = oracle_mod.icd(x0.astype(np.float64), 3, cS, tol=1e-12, max_sweeps=3000)
+    assert err(got, ref.x) <= TOL, err(got, ref.x)
+
+
+# ------------------------------------------------------------ bounds
+
+def test_maxstat_bounds_match_oracle(smre, torch_cuda, oracle_mod):
+    H, W, sides, draws, seed = 12, 10, [1, 2, 3], 200, 77
+    p = smre.make_params(H, W, sides, alpha=0.9, cmode=smre.SMRE_C_MAXSTAT,
+                         maxstat_draws=draws, seed=seed)
+    got = np.array(smre.smre_bounds(p))
+    ref = oracle_mod.bounds(sides, 0.9, "maxstat", H=H, W=W, draws=draws, seed=seed)
+    assert np.allclose(got, ref, rtol=1e-4), (got, ref)
+
+
+def test_errors_on_device(smre, torch_cuda):
+    with smre.Projector(16, 16, [1, 2]) as P:
+        x = torch_cuda.zeros(16, 16, device="cuda")
+        with pytest.raises(smre.SmreError):
+            P.project_incomplete(x, x, K=6)
+        with pytest.raises(smre.SmreError):
+            P.project_incomplete(x, x, K=5)      # tile 32 > image
+        assert P.device_bytes() > 0
