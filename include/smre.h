@@ -154,6 +154,10 @@ SMRE_API smre_status smre_dykstra_history(smre_dykstra *h, double *out, int n_ma
  * the total; at most n_max values are copied. */
 SMRE_API smre_status smre_dykstra_icd_sweeps(smre_dykstra *h, int *out, int n_max, int *n_tiles);
 
+/* Number of kernels the handle has launched since it was created (every
+ * launch of every entry point; a monotone counter kept on the host). */
+SMRE_API long long smre_dykstra_kernel_launches(const smre_dykstra *h);
+
 /* Bytes of device memory the handle holds. */
 SMRE_API size_t smre_dykstra_device_bytes(const smre_dykstra *h);
 

@@ -24,6 +24,7 @@ __all__ = [
     "smre_dykstra_project_incomplete", "smre_dykstra_set_stopping", "smre_dykstra_bounds",
     "smre_dykstra_history", "smre_dykstra_icd_sweeps", "smre_dykstra_device_bytes",
     "smre_dykstra_destroy", "smre_last_error", "smre_version", "Projector", "EXPORTED",
+    "smre_dykstra_kernel_launches", "make_params",
 ]
 
 SMRE_OK, SMRE_EINVAL, SMRE_ENOMEM, SMRE_ECUDA, SMRE_ETIMEOUT, SMRE_ENOTCONVERGED = range(6)
@@ -37,7 +38,7 @@ EXPORTED = (
     "smre_bounds", "smre_dykstra_create", "smre_dykstra_project",
     "smre_dykstra_project_incomplete", "smre_dykstra_set_stopping", "smre_dykstra_bounds",
     "smre_dykstra_history", "smre_dykstra_icd_sweeps", "smre_dykstra_device_bytes",
-    "smre_dykstra_destroy", "smre_last_error", "smre_version",
+    "smre_dykstra_destroy", "smre_last_error", "smre_version", "smre_dykstra_kernel_launches",
 )
 
 
@@ -104,6 +105,7 @@ def load():
         "smre_dykstra_history": (st, [H, P(ctypes.c_double), ctypes.c_int, P(ctypes.c_int)]),
         "smre_dykstra_icd_sweeps": (st, [H, P(ctypes.c_int), ctypes.c_int, P(ctypes.c_int)]),
         "smre_dykstra_device_bytes": (ctypes.c_size_t, [H]),
+        "smre_dykstra_kernel_launches": (ctypes.c_longlong, [H]),
         "smre_dykstra_destroy": (None, [H]),
         "smre_last_error": (ctypes.c_char_p, [H]),
         "smre_version": (ctypes.c_char_p, []),
@@ -249,6 +251,10 @@ def smre_dykstra_device_bytes(h) -> int:
     return int(load().smre_dykstra_device_bytes(h))
 
 
+def smre_dykstra_kernel_launches(h) -> int:
+    return int(load().smre_dykstra_kernel_launches(h))
+
+
 def smre_dykstra_destroy(h):
     load().smre_dykstra_destroy(h)
 
@@ -280,6 +286,9 @@ class Projector:
 
     def device_bytes(self):
         return smre_dykstra_device_bytes(self.h)
+
+    def kernel_launches(self):
+        return smre_dykstra_kernel_launches(self.h)
 
     def close(self):
         if self.h:

@@ -54,6 +54,7 @@ struct smre_dykstra {
     double *viol_host = nullptr;   // pinned
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     size_t dev_bytes = 0;
+    long long launches = 0;
     std::string err;
 };
 
@@ -273,6 +274,7 @@ smre_status violation(smre_dykstra *h, double &out)
         va.cS[i] = h->cS[i];
     }
     CK(h, launch_violation(va, h->partials, h->n_partials, h->viol, h->stream));
+    h->launches += 2;
     CK(h, cudaMemcpyAsync(h->viol_host, h->viol, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     out = *h->viol_host;
@@ -419,11 +421,13 @@ smre_status smre_dykstra_project(smre_dykstra *h, const float *x0, float *x, smr
             A.cS64 = h->cS_of[g.L];
             A.first = cyc == 0;
             CK(h, launch_group(A, h->stream));
+            h->launches += g.n_units > 0;
         }
         CK(h, launch_cycle_norm(h->xw, h->xprev, h->H, h->W, h->pitch, h->partials,
                                 h->n_partials, h->stream));
         CK(h, launch_decide(h->partials, h->n_partials, h->ctl, h->hist, h->hist_cap, h->tol,
                             h->tol_relative, h->stream));
+        h->launches += 2;
         CK(h, cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(Control), cudaMemcpyDeviceToHost,
                               h->stream));
         CK(h, cudaStreamSynchronize(h->stream));
@@ -522,6 +526,7 @@ smre_status smre_dykstra_project_incomplete(smre_dykstra *h, const float *x0, fl
         }
         A.sweeps = h->icd_sweeps + o;
         CK(h, launch_icd_pass(A, h->stream));
+        h->launches += ni[i] * nj[i] > 0;
         o += ni[i] * nj[i];
     }
     CK(h, cudaEventRecord(h->ev1, h->stream));
@@ -602,6 +607,8 @@ smre_status smre_dykstra_icd_sweeps(smre_dykstra *h, int *out, int n_max, int *n
 }
 
 size_t smre_dykstra_device_bytes(const smre_dykstra *h) { return h ? h->dev_bytes : 0; }
+
+long long smre_dykstra_kernel_launches(const smre_dykstra *h) { return h ? h->launches : 0; }
 
 void smre_dykstra_destroy(smre_dykstra *h)
 {
