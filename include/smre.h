@@ -71,7 +71,15 @@ typedef enum {
 } smre_cmode;
 
 /* flags */
-#define SMRE_F_VIOLATION 1  /* fill smre_result.max_violation (one extra pass)   */
+#define SMRE_F_VIOLATION 1        /* fill smre_result.max_violation (one extra pass)   */
+#define SMRE_F_GROUP_LAUNCHES 2   /* run the standard method as one kernel launch per
+                                     (side, row offset) group with a host-side stop
+                                     check per cycle, instead of the single persistent
+                                     cooperative launch (same results, slower)        */
+#define SMRE_F_SELFTEST_TIMEOUT 4 /* testing aid: the persistent launch additionally
+                                     waits on a flag nothing sets, with a 50 ms limit,
+                                     so smre_dykstra_project must return
+                                     SMRE_ETIMEOUT and the handle stay usable        */
 
 typedef struct {
     int height, width;          /* pixels: 1 <= height <= 65535, 1 <= width <= 4096 */

@@ -19,6 +19,7 @@ import os
 __all__ = [
     "SMRE_OK", "SMRE_EINVAL", "SMRE_ENOMEM", "SMRE_ECUDA", "SMRE_ETIMEOUT", "SMRE_ENOTCONVERGED",
     "SMRE_C_PERSET", "SMRE_C_CHI2", "SMRE_C_MAXSTAT", "SMRE_C_EXPLICIT", "SMRE_F_VIOLATION",
+    "SMRE_F_GROUP_LAUNCHES", "SMRE_F_SELFTEST_TIMEOUT",
     "SmreError", "smre_params", "smre_result", "lib_path", "load",
     "smre_bounds", "smre_dykstra_create", "smre_dykstra_project",
     "smre_dykstra_project_incomplete", "smre_dykstra_set_stopping", "smre_dykstra_bounds",
@@ -30,6 +31,8 @@ __all__ = [
 SMRE_OK, SMRE_EINVAL, SMRE_ENOMEM, SMRE_ECUDA, SMRE_ETIMEOUT, SMRE_ENOTCONVERGED = range(6)
 SMRE_C_PERSET, SMRE_C_CHI2, SMRE_C_MAXSTAT, SMRE_C_EXPLICIT = range(4)
 SMRE_F_VIOLATION = 1
+SMRE_F_GROUP_LAUNCHES = 2
+SMRE_F_SELFTEST_TIMEOUT = 4
 
 _STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENOTCONVERGED"}
 

@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(1024, 1) group_kernel(const GroupArgs A)
                 float ts = 0.f;
                 for (int jj = 0; jj < L; ++jj) ts += part[v0[j] + jj];
                 if (fabsf(ts - A.cS) <= kNearBand * A.cS) near = true;
-                if (ts > A.cS) scale[j] = sqrtf(A.cS / ts);
+                if (ts > A.cS) scale[j] = A.sqrt_cS * rsqrtf(ts);
             }
         }
         if (__syncthreads_or(near)) {

@@ -7,7 +7,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <cstdlib>
 #include <new>
+#include <type_traits>
 #include <string>
 #include <vector>
 
@@ -55,6 +57,19 @@ struct smre_dykstra {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     size_t dev_bytes = 0;
     long long launches = 0;
+    // persistent path plan
+    bool persist = false;
+    int p_grid = 0, p_threads = 0, p_stages = 0, p_ncw = 0, p_maxL = 0;
+    size_t p_smem = 0;
+    int p_stage_floats = 0, p_stage_offset = 0;
+    int n_tasks = 0;
+    unsigned char *d_sched = nullptr;
+    int4 *d_cta_sched = nullptr;
+    int p_sched_bytes = 0;
+    unsigned *d_flags = nullptr, *d_barrier = nullptr, *d_selftest = nullptr;
+    double *d_ppartials = nullptr;
+    int *d_abort = nullptr;
+    unsigned long long timeout_ns = 10000000000ull;
     std::string err;
 };
 
@@ -281,6 +296,215 @@ smre_status violation(smre_dykstra *h, double &out)
     return SMRE_OK;
 }
 
+// Plan of the persistent kernel: home bands of rows per CTA, tasks, the flags
+// each task waits for, the last toucher of every row, and the stage ring.
+// Leaves h->persist false when the shape does not fit it (the group-launch
+// path then runs instead).
+smre_status plan_persistent(smre_dykstra *h, int flags)
+{
+    h->persist = false;
+    if (flags & SMRE_F_GROUP_LAUNCHES) return SMRE_OK;
+    int dev = 0, sms = 0, smem_optin = 0;
+    CK(h, cudaGetDevice(&dev));
+    CK(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CK(h, cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    const int H = h->H, W = h->W, pitch = h->pitch;
+    const int G = std::max(1, std::min(sms, H));
+    auto owner = [&](int r) { return (int)(((long long)r * G) / H); };
+
+    // tasks per (group, CTA), in cycle order
+    struct T0 { int g, c, ub, ue; };
+    std::vector<T0> tasks;
+    for (int g = 0; g < (int)h->groups.size(); ++g) {
+        const Group &gr = h->groups[g];
+        int u = 0;
+        while (u < gr.n_units) {
+            const int c = owner(gr.a + gr.L * u);
+            int v = u + 1;
+            while (v < gr.n_units && owner(gr.a + gr.L * v) == c) ++v;
+            tasks.push_back({g, c, u, v});
+            u = v;
+        }
+    }
+    // dependencies on the last toucher of each row (other CTAs only)
+    std::vector<int> last(H, -1);
+    std::vector<std::vector<int>> deps(tasks.size());
+    size_t t = 0;
+    while (t < tasks.size()) {
+        size_t e = t;
+        while (e < tasks.size() && tasks[e].g == tasks[t].g) ++e;
+        for (size_t k = t; k < e; ++k) {
+            const Group &gr = h->groups[tasks[k].g];
+            const int r0 = gr.a + gr.L * tasks[k].ub, r1 = gr.a + gr.L * tasks[k].ue;
+            for (int r = r0; r < r1; ++r) {
+                const int d = last[r];
+                if (d >= 0 && tasks[d].c != tasks[k].c &&
+                    std::find(deps[k].begin(), deps[k].end(), d) == deps[k].end())
+                    deps[k].push_back(d);
+            }
+        }
+        for (size_t k = t; k < e; ++k) {
+            const Group &gr = h->groups[tasks[k].g];
+            for (int r = gr.a + gr.L * tasks[k].ub; r < gr.a + gr.L * tasks[k].ue; ++r) last[r] = (int)k;
+        }
+        t = e;
+    }
+    // order tasks by (CTA, cycle order) and renumber
+    std::vector<int> order(tasks.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return tasks[a].c < tasks[b].c; });
+    std::vector<int> newid(tasks.size());
+    for (size_t i = 0; i < order.size(); ++i) newid[order[i]] = (int)i;
+    std::vector<int> final_task(H, -1);
+    for (int r = 0; r < H; ++r)
+        if (last[r] >= 0) final_task[r] = newid[last[r]];
+
+    // per-CTA schedule segments: TaskS[] | pass q offsets | dependency ids
+    std::vector<unsigned char> sched;
+    std::vector<int4> cta_sched(G);
+    int maxL = 0, max_items = 1;
+    long long stage_floats = 0;
+    size_t seg_max = 16;
+    size_t i = 0;
+    for (int c = 0; c < G; ++c) {
+        std::vector<TaskS> ts;
+        std::vector<long long> qo;
+        std::vector<int> dl;
+        for (; i < order.size() && tasks[order[i]].c == c; ++i) {
+            const T0 &o = tasks[order[i]];
+            const Group &gr = h->groups[o.g];
+            TaskS t{};
+            t.L = gr.L;
+            t.U = o.ue - o.ub;
+            t.r_first = gr.a + gr.L * o.ub;
+            t.gid = (int)i;
+            t.dep_begin = (int)dl.size();
+            for (int d : deps[order[i]]) dl.push_back(newid[d]);
+            t.dep_count = (int)dl.size() - t.dep_begin;
+            t.pass0 = (int)qo.size();
+            t.cS = (float)h->cS_of[gr.L];
+            t.sqrt_cS = (float)std::sqrt(h->cS_of[gr.L]);
+            t.cS64 = h->cS_of[gr.L];
+            t.final_mask = 0;
+            for (int r = t.r_first; r < t.r_first + t.U * t.L; ++r)
+                if (final_task[r] == (int)i) t.final_mask |= 1ull << (r - t.r_first);
+            for (int bb = 0; bb < gr.L; ++bb)
+                qo.push_back(h->tilings[gr.tiling0 + bb].q_off + (long long)o.ub * gr.L * pitch);
+            maxL = std::max(maxL, t.L);
+            {
+                const int wpw = 32 / t.L, nv = W / t.L;
+                max_items = std::max(max_items, t.U * ((nv + wpw - 1) / wpw));
+            }
+            stage_floats = std::max(stage_floats, (long long)t.U * t.L * pitch);
+            if (t.U * t.L > 64) return SMRE_OK;   // row mask would not fit
+            ts.push_back(t);
+        }
+        const size_t bytes = sizeof(TaskS) * ts.size() + sizeof(long long) * qo.size() +
+                             sizeof(int) * dl.size();
+        const size_t padded = (bytes + 15) / 16 * 16;
+        cta_sched[c] = make_int4((int)sched.size(), (int)ts.size(), (int)qo.size(), (int)dl.size());
+        const size_t at = sched.size();
+        sched.resize(at + std::max<size_t>(padded, 16), 0);
+        unsigned char *w = sched.data() + at;
+        memcpy(w, ts.data(), sizeof(TaskS) * ts.size());
+        w += sizeof(TaskS) * ts.size();
+        memcpy(w, qo.data(), sizeof(long long) * qo.size());
+        w += sizeof(long long) * qo.size();
+        memcpy(w, dl.data(), sizeof(int) * dl.size());
+        seg_max = std::max(seg_max, padded);
+    }
+
+    if (!persist_supported(maxL)) return SMRE_OK;
+    const int ncw = std::max(4, std::min(kPersistThreads / 32 - 1, max_items));
+    if (max_items > kMaxItems * ncw) return SMRE_OK;   // too many items per warp
+    const int threads = (ncw + 1) * 32;
+    const size_t xs_bytes = (size_t)stage_floats * 4;   // the largest task's rows
+    const size_t stage_offset = 512 + (seg_max + 127) / 128 * 128;
+    const size_t budget = (size_t)smem_optin - 1024;   // static shared memory and slack
+    if (budget < stage_offset + xs_bytes) return SMRE_OK;
+    const long long fit = (long long)((budget - stage_offset - xs_bytes) / (stage_floats * 4));
+    const int S = (int)std::min<long long>(kMaxStages, fit);
+    if (S < 3) return SMRE_OK;
+    const size_t smem = stage_offset + (size_t)S * stage_floats * 4 + xs_bytes;
+    int occ = 0;
+    cudaError_t oe = persist_occupancy(maxL, threads, smem, &occ);
+    if (oe != cudaSuccess || occ < 1) {
+        cudaGetLastError();
+        return SMRE_OK;
+    }
+
+    auto up = [&](auto **dptr, const auto &vec) -> cudaError_t {
+        using E = typename std::remove_reference<decltype(vec[0])>::type;
+        const size_t bytes = sizeof(E) * std::max<size_t>(vec.size(), 1);
+        cudaError_t e = cudaMalloc((void **)dptr, bytes);
+        if (e != cudaSuccess) return e;
+        h->dev_bytes += bytes;
+        return cudaMemcpy(*dptr, vec.data(), sizeof(E) * vec.size(), cudaMemcpyHostToDevice);
+    };
+    CK(h, up(&h->d_sched, sched));
+    CK(h, up(&h->d_cta_sched, cta_sched));
+    CK(h, cudaMalloc(&h->d_flags, sizeof(unsigned) * std::max<size_t>(tasks.size(), 1)));
+    CK(h, cudaMalloc(&h->d_barrier, 64));
+    CK(h, cudaMalloc(&h->d_selftest, 64));
+    CK(h, cudaMemset(h->d_selftest, 0, 64));
+    CK(h, cudaMalloc(&h->d_abort, 64));
+    CK(h, cudaMalloc(&h->d_ppartials, sizeof(double) * 4 * G));
+    h->dev_bytes += sizeof(unsigned) * tasks.size() + 192 + sizeof(double) * 4 * G;
+    h->n_tasks = (int)tasks.size();
+    h->p_grid = G;
+    h->p_threads = threads;
+    h->p_stages = S;
+    h->p_ncw = ncw;
+    h->p_maxL = maxL;
+    h->p_smem = smem;
+    h->p_stage_floats = (int)stage_floats;
+    h->p_stage_offset = (int)stage_offset;
+    h->p_sched_bytes = (int)seg_max;
+    if (const char *env = getenv("SMRE_WAIT_TIMEOUT_MS")) {
+        const double ms = atof(env);
+        if (ms > 0) h->timeout_ns = (unsigned long long)(ms * 1e6);
+    }
+    h->persist = true;
+    return SMRE_OK;
+}
+
+smre_status run_persistent(smre_dykstra *h)
+{
+    CK(h, cudaMemsetAsync(h->d_flags, 0, sizeof(unsigned) * std::max(h->n_tasks, 1), h->stream));
+    CK(h, cudaMemsetAsync(h->d_barrier, 0, 64, h->stream));
+    CK(h, cudaMemsetAsync(h->d_abort, 0, 64, h->stream));
+    PersistArgs A{};
+    A.x = h->xw;
+    A.xprev = h->xprev;
+    A.q = h->q;
+    A.pitch = h->pitch;
+    A.H = h->H;
+    A.W = h->W;
+    A.consumer_warps = h->p_ncw;
+    A.sched = h->d_sched;
+    A.cta_sched = h->d_cta_sched;
+    A.sched_bytes = h->p_sched_bytes;
+    A.flags = h->d_flags;
+    A.barrier = h->d_barrier;
+    A.partials = h->d_ppartials;
+    A.ctl = h->ctl;
+    A.hist = h->hist;
+    A.hist_cap = h->hist_cap;
+    A.max_cycles = h->max_cycles;
+    A.tol = h->tol;
+    A.tol_relative = h->tol_relative;
+    A.stages = h->p_stages;
+    A.stage_floats = h->p_stage_floats;
+    A.stage_offset = h->p_stage_offset;
+    A.timeout_ns = (h->flags & SMRE_F_SELFTEST_TIMEOUT) ? 50000000ull : h->timeout_ns;
+    A.abort_word = h->d_abort;
+    A.selftest_timeout = (h->flags & SMRE_F_SELFTEST_TIMEOUT) ? 1 : 0;
+    A.selftest_flag = h->d_selftest;
+    CK(h, launch_persist(A, h->p_maxL, h->p_grid, h->p_threads, h->p_smem, h->stream));
+    h->launches += 1;
+    return SMRE_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -375,6 +599,7 @@ smre_status smre_dykstra_create(const smre_params *p, void *cuda_stream, smre_dy
     h->dev_bytes = sizeof(float) * std::max<size_t>(h->q_floats, 1) + 2 * img +
                    sizeof(double) * 2 * h->n_partials + sizeof(Control) + sizeof(double);
     if (ensure_hist(h, h->max_cycles) != SMRE_OK) return bail(SMRE_ENOMEM);
+    if (plan_persistent(h, p->flags) != SMRE_OK) return bail(SMRE_ECUDA);
 #undef CKC
     *out = h;
     return SMRE_OK;
@@ -405,7 +630,15 @@ smre_status smre_dykstra_project(smre_dykstra *h, const float *x0, float *x, smr
     CK(h, cudaEventRecord(h->ev0, h->stream));
 
     int cycles = 0;
-    for (int cyc = 0; cyc < h->max_cycles; ++cyc) {
+    if (h->persist) {
+        st = run_persistent(h);
+        if (st != SMRE_OK) return st;
+        CK(h, cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(Control), cudaMemcpyDeviceToHost,
+                              h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+        cycles = h->ctl_host->cycles;
+    }
+    for (int cyc = 0; !h->persist && cyc < h->max_cycles; ++cyc) {
         for (const Group &g : h->groups) {
             GroupArgs A{};
             A.x = h->xw;
@@ -418,6 +651,7 @@ smre_status smre_dykstra_project(smre_dykstra *h, const float *x0, float *x, smr
             A.a = g.a;
             A.n_units = g.n_units;
             A.cS = (float)h->cS_of[g.L];
+            A.sqrt_cS = (float)std::sqrt(h->cS_of[g.L]);
             A.cS64 = h->cS_of[g.L];
             A.first = cyc == 0;
             CK(h, launch_group(A, h->stream));
@@ -622,6 +856,13 @@ void smre_dykstra_destroy(smre_dykstra *h)
     cudaFree(h->ctl);
     cudaFree(h->icd_sweeps);
     cudaFree(h->viol);
+    cudaFree(h->d_sched);
+    cudaFree(h->d_cta_sched);
+    cudaFree(h->d_flags);
+    cudaFree(h->d_barrier);
+    cudaFree(h->d_selftest);
+    cudaFree(h->d_abort);
+    cudaFree(h->d_ppartials);
     if (h->ctl_host) cudaFreeHost(h->ctl_host);
     if (h->viol_host) cudaFreeHost(h->viol_host);
     if (h->ev0) cudaEventDestroy(h->ev0);

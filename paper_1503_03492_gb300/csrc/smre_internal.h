@@ -50,9 +50,74 @@ struct GroupArgs {
     int pitch, H, W;
     int L, a, n_units;
     float cS;             // bound of side L (FP32 copy for the fast test)
+    float sqrt_cS;        // sqrt(cS) in FP32: scale = sqrt(cS) * rsqrt(t)
     double cS64;          // the same bound in FP64 for the near-boundary recheck
     int first;            // 1: first cycle, stored increments are taken as 0
 };
+
+// ---- persistent standard path (smre_persist.cu)
+
+constexpr int kMaxStages = 16;    // ring stages of the increment stream
+constexpr int kPersistThreads = 640;   // most threads per CTA of the persistent kernel
+constexpr int kMaxItems = 4;          // (unit, window chunk) items per consumer warp and task
+
+// Task = the units of one group owned by one CTA (a contiguous row band).
+struct TaskDesc {
+    int g;                // group index in the cycle order
+    int ub, ue;           // unit range [ub, ue)
+    int dep_begin, dep_count;   // flags (task ids) to wait for, in deps[]
+};
+
+struct GroupDesc {
+    int L, a, tiling0;
+    float cS;
+    double cS64;
+};
+
+// Per-CTA schedule entry kept in shared memory for the whole launch.
+struct TaskS {
+    int r_first;                  // first image row of the task's units
+    int L, U;                     // side and number of units
+    int gid;                      // global task id (index of its flag)
+    int dep_begin, dep_count;     // range in the CTA's dependency list
+    int pass0;                    // first entry in the CTA's pass table
+    float cS;
+    float sqrt_cS;                // sqrt(cS) in FP32: scale = sqrt(cS) * rsqrt(t)
+    int pad_;
+    unsigned long long final_mask;  // bit j*L+i: row r_first+j*L+i is final in this task
+    double cS64;
+};
+
+struct PersistArgs {
+    float *x, *xprev, *q;
+    int pitch, H, W;
+    int consumer_warps;          // warps 0..consumer_warps-1 consume, the next one produces
+    // per-CTA schedule: TaskS[n_tasks] | long long pass_qoff[n_passes] | int deps[n_deps]
+    const unsigned char *sched;
+    const int4 *cta_sched;       // [G]: byte offset, n_tasks, n_passes, n_deps
+    int sched_bytes;             // shared-memory bytes reserved for the largest segment
+    unsigned *flags;             // [n_tasks] cycle + 1 once the task is done
+    unsigned *barrier;           // grid barrier counter
+    double *partials;            // [2][G][2] per-CTA norms, double-buffered by cycle
+    Control *ctl;
+    double *hist;
+    int hist_cap;
+    int max_cycles;
+    double tol;
+    int tol_relative;
+    int stages;
+    int stage_floats;            // floats per stage
+    int stage_offset;            // bytes from the start of dynamic shared memory
+    unsigned long long timeout_ns;
+    int *abort_word;
+    int selftest_timeout;
+    const unsigned *selftest_flag;
+};
+
+bool persist_supported(int max_side);
+cudaError_t persist_occupancy(int max_side, int threads, size_t smem, int *blocks_per_sm);
+cudaError_t launch_persist(const PersistArgs &A, int max_side, int grid, int threads, size_t smem,
+                           cudaStream_t s);
 
 // Launchers (defined next to their kernels).
 cudaError_t launch_group(const GroupArgs &args, cudaStream_t s);

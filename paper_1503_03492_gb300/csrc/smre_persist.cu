@@ -1,0 +1,631 @@
+// Persistent cooperative kernel of the standard Dykstra path on sm_103a.
+//
+// One launch runs the whole projection (Sec. 2.3, Algorithm 2): every cycle
+// visits the groups (L, a) in the set order (sides descending, a ascending);
+// inside a group the L tilings (L, a, b), b = 0..L-1, only move windows
+// sideways, so a CTA that owns a band of window-rows ("units") of the group
+// runs all L passes on it with block barriers alone.  Ownership follows
+// fixed home bands of image rows, so consecutive groups of a CTA overlap and
+// most ordering is program order; a task (group, CTA) waits only for the
+// flags of the other CTAs' tasks that last touched its rows.  One grid barrier
+// per cycle gathers the FP64 norms of the stopping test.
+//
+// Data movement:
+//  - increments q_s (the HBM stream, sum_L L^2 H W floats) move between HBM
+//    and a ring of shared-memory stages with bulk async copies (TMA engine):
+//    one elected thread keeps S-2 passes of loads in flight ahead of the
+//    consumers and writes each pass's updated increments back with a bulk
+//    store, so the copy engine streams while the CTA waits or computes;
+//  - x of the CTA's rows sits in registers for the L passes of a task; it goes
+//    through L2 only at task boundaries;
+//  - the cycle norm |x - x_prev|^2, |x_prev|^2 (FP64) is fused into the task
+//    that last touches each row in a cycle.
+//
+// Every wait (dependency flags, grid barrier, copy completion) has a time
+// limit; on expiry the kernel records SMRE_ETIMEOUT, lets its copies in
+// flight finish, and returns, so the context stays usable.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "smre_internal.h"
+
+namespace smre {
+
+namespace {
+
+constexpr float kNearBand = 1e-6f;
+
+// ---------------------------------------------------------------- PTX helpers
+
+__device__ __forceinline__ unsigned smem_u32(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void bulk_load(void *dst_smem, const void *src, unsigned bytes,
+                                          uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst_smem)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void bulk_store(void *dst, const void *src_smem, unsigned bytes)
+{
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst),
+                 "r"(smem_u32(src_smem)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+
+__device__ __forceinline__ void bulk_wait_read1()
+{
+    asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+}
+
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(unsigned *p, unsigned v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long globaltimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ int ld_volatile(const int *p) { return *(volatile const int *)p; }
+
+// Record a time-out once and raise the abort word every CTA polls.
+__device__ void raise_timeout(const PersistArgs &A)
+{
+    atomicCAS(&A.ctl->status, (int)SMRE_OK, (int)SMRE_ETIMEOUT);
+    atomicExch(A.abort_word, 1);
+}
+
+// Thread 0: wait until *p >= target (acquire), or time out / see an abort.
+// Returns false when the CTA must abandon the projection.
+__device__ bool wait_geq(const PersistArgs &A, const unsigned *p, unsigned target)
+{
+    if (ld_acquire(p) >= target) return true;
+    const unsigned long long t0 = globaltimer();
+    for (unsigned it = 0;; ++it) {
+        if (ld_acquire(p) >= target) return true;
+        if ((it & 63) == 63) {
+            if (ld_volatile(A.abort_word)) return false;
+            if (globaltimer() - t0 > A.timeout_ns) {
+                raise_timeout(A);
+                return false;
+            }
+            __nanosleep(64);
+        }
+    }
+}
+
+// Wait on an mbarrier phase with a time limit (every wait of the kernel is
+// bounded).  Returns false on time-out or when another CTA aborted.
+__device__ bool mbar_wait_timed(const PersistArgs &A, uint64_t *bar, unsigned parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer();
+    for (unsigned it = 0;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 255) == 255) {
+            if (ld_volatile(A.abort_word)) return false;
+            if (globaltimer() - t0 > A.timeout_ns) {
+                raise_timeout(A);
+                return false;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void bulk_wait_read0()
+{
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+
+// named barrier 1 among the consumer warps; returns the OR of pred over them
+__device__ __forceinline__ bool consumers_sync_or(bool pred, int nthreads)
+{
+    unsigned r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "barrier.red.or.pred q, 1, %2, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((unsigned)pred), "r"(nthreads)
+        : "memory");
+    return r != 0;
+}
+
+__device__ __forceinline__ void consumers_sync(int nthreads)
+{
+    asm volatile("barrier.sync 1, %0;" ::"r"(nthreads) : "memory");
+}
+
+__device__ __forceinline__ void cta_sync_all() { asm volatile("barrier.sync 0;" ::: "memory"); }
+
+enum { kGo = 0, kStop = 1, kAbort = 2 };
+
+// ------------------------------------------------------------------ kernel
+//
+// Warps 0 .. NCW-1 consume: they run the projections of each pass.  Warp NCW
+// produces: its lane 0 streams the increments through the stage ring.
+//   full[s]    completes when stage s holds the increments of its next pass
+//              (bulk load; in the first cycle q = 0 and a plain arrive only
+//              hands the empty stage over)
+//   written[s] completes when every consumer warp has written the pass's new
+//              increments into stage s, so the producer can store them and
+//              then refill the stage S passes ahead.
+// In pass b of a task the consumer lanes map onto windows: with
+// wpw = floor(32 / L) windows per warp, lane l takes column l % L of window
+// k * wpw + l / L of its warp's chunk k; a window's column sums meet by
+// shuffles in a fixed order, so every lane of a window sees the same sum.
+// x of the task's rows lives in shared memory for the task's L passes.
+template <int LB>
+__global__ void __launch_bounds__(kPersistThreads, 1) persist_kernel(const PersistArgs A)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int S = A.stages;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem);              // [S]
+    uint64_t *written = full + kMaxStages;                            // [S]
+    int *s_prov = reinterpret_cast<int *>(written + kMaxStages);      // [S] provides per stage
+    unsigned char *tbl = smem + 512;                                  // schedule
+    float *stage0 = reinterpret_cast<float *>(smem + A.stage_offset); // [S][stage_floats]
+    float *xs = stage0 + (size_t)S * A.stage_floats;                  // [rows][pitch]
+    __shared__ int s_dec, s_abort;
+    __shared__ double s_red[2][32];
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int NCW = A.consumer_warps, NC = NCW * 32;
+    const int cta = blockIdx.x, G = gridDim.x;
+    const int pitch = A.pitch;
+
+    const int4 seg = A.cta_sched[cta];
+    const int ntask = seg.y, npass = seg.z, ndep = seg.w;
+    {
+        const int4 *src = reinterpret_cast<const int4 *>(A.sched + seg.x);
+        int4 *dst = reinterpret_cast<int4 *>(tbl);
+        const int n16 = (int)((sizeof(TaskS) * ntask + sizeof(long long) * npass +
+                               sizeof(int) * ndep + 15) / 16);
+        for (int i = tid; i < n16; i += blockDim.x) dst[i] = src[i];
+    }
+    const TaskS *tasks_s = reinterpret_cast<const TaskS *>(tbl);
+    const long long *pass_qoff = reinterpret_cast<const long long *>(tasks_s + ntask);
+    const int *deps_s = reinterpret_cast<const int *>(pass_qoff + npass);
+
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&written[s], (unsigned)NCW);
+            s_prov[s] = 0;
+        }
+        fence_mbar_init();
+        s_dec = kGo;
+        s_abort = 0;
+    }
+    __syncthreads();
+
+    if (warp == NCW) {
+        // ===================================================== producer warp
+        bool dead = false;
+        int s_head = 0;        // stage of the next pass to store
+        unsigned wph = 0;      // parity of the next `written` wait, per stage
+        for (int cyc = 0;; ++cyc) {
+            const bool first = cyc == 0;
+            if (lane == 0 && npass > 0 && !dead) {
+                auto provide = [&](int task, int b, int stg) {
+                    s_prov[stg] += 1;
+                    if (first) {
+                        mbar_arrive(&full[stg]);
+                        return;
+                    }
+                    const TaskS &ts = tasks_s[task];
+                    const unsigned unit_bytes = (unsigned)(ts.L * pitch * sizeof(float));
+                    mbar_arrive_expect_tx(&full[stg], unit_bytes * ts.U);
+                    const float *src = A.q + pass_qoff[ts.pass0 + b];
+                    float *dst = stage0 + (size_t)stg * A.stage_floats;
+                    for (int j = 0; j < ts.U; ++j)
+                        bulk_load(dst + (size_t)j * ts.L * pitch, src + (size_t)j * ts.L * pitch,
+                                  unit_bytes, &full[stg]);
+                };
+                int rt = 0, rb = 0, rs = s_head;       // refill cursor
+                const int pre = npass < S ? npass : S;
+                for (int k = 0; k < pre; ++k) {
+                    provide(rt, rb, rs);
+                    if (++rb == tasks_s[rt].L) { rb = 0; ++rt; }
+                    rs = rs + 1 == S ? 0 : rs + 1;
+                }
+                int t = 0, bb = 0;                     // store cursor
+                for (int p = 0; p < npass; ++p) {
+                    if (!mbar_wait_timed(A, &written[s_head], (wph >> s_head) & 1u)) {
+                        dead = true;
+                        break;
+                    }
+                    wph ^= 1u << s_head;
+                    const TaskS &ts = tasks_s[t];
+                    const unsigned unit_bytes = (unsigned)(ts.L * pitch * sizeof(float));
+                    float *dq = A.q + pass_qoff[ts.pass0 + bb];
+                    const float *sq = stage0 + (size_t)s_head * A.stage_floats;
+                    for (int j = 0; j < ts.U; ++j)
+                        bulk_store(dq + (size_t)j * ts.L * pitch, sq + (size_t)j * ts.L * pitch,
+                                   unit_bytes);
+                    bulk_commit();
+                    if (p + S < npass) {
+                        bulk_wait_read0();     // the store has read the stage out
+                        provide(rt, rb, s_head);
+                        if (++rb == tasks_s[rt].L) { rb = 0; ++rt; }
+                    }
+                    if (++bb == ts.L) { bb = 0; ++t; }
+                    s_head = s_head + 1 == S ? 0 : s_head + 1;
+                }
+                bulk_wait_all();               // this cycle's stores have landed
+            }
+            __syncwarp();
+            cta_sync_all();                    // consumers publish the decision
+            const int dec = s_dec;
+            cta_sync_all();
+            if (dec != kGo || dead) break;
+        }
+        if (lane == 0) {
+            // let every load in flight land before the shared memory is released
+            for (int s = 0; s < S; ++s) {
+                if (s_prov[s] == 0) continue;
+                const unsigned par = (unsigned)((s_prov[s] - 1) & 1);
+                for (unsigned it = 0; !mbar_try_wait(&full[s], par) && it < (1u << 22); ++it) {
+                }
+            }
+            bulk_wait_all();
+        }
+        return;
+    }
+
+    // ======================================================== consumer warps
+    int s_cur = 0;
+    unsigned fph = 0;            // parity of the next `full` wait, per stage
+    double d2 = 0.0, n2 = 0.0;   // this thread's share of the cycle norm
+    bool aborted = false;
+
+    for (int cyc = 0;; ++cyc) {
+        const bool first = cyc == 0;
+        for (int ti = 0; ti < ntask && !aborted; ++ti) {
+            const TaskS ts = tasks_s[ti];
+            const int L = ts.L, U = ts.U;
+            const int rows = U * L;
+
+            // wait for the other CTAs' tasks that last touched these rows
+            if (tid == 0) {
+                bool ok = true;
+                if (A.selftest_timeout && cta == 0 && ti == 0)
+                    ok = wait_geq(A, A.selftest_flag, 1u);   // a flag nothing sets
+                for (int k = 0; k < ts.dep_count && ok; ++k)
+                    ok = wait_geq(A, A.flags + deps_s[ts.dep_begin + k], (unsigned)(cyc + 1));
+                s_abort = ok ? 0 : 1;
+            }
+            consumers_sync(NC);
+            if (s_abort) { aborted = true; break; }
+
+            // x rows of the task into shared memory (from L2)
+            {
+                const float4 *src = reinterpret_cast<const float4 *>(A.x + (size_t)ts.r_first * pitch);
+                float4 *dst = reinterpret_cast<float4 *>(xs);
+                const int n4 = rows * pitch / 4;
+                for (int i = tid; i < n4; i += NC) dst[i] = __ldcg(src + i);
+            }
+            consumers_sync(NC);
+
+            const int wpw = 32 / L;                  // windows per warp
+            const int wl = lane / L, col = lane - wl * L;   // window of the lane, column in it
+            const bool lane_on = lane < wpw * L;
+            const int nv0 = A.W / L, rem0 = A.W - nv0 * L;  // windows of pass b: nv0 - (b > rem0)
+            const int nwc = (nv0 + wpw - 1) / wpw;          // warp chunks per unit
+            // this warp's (unit, chunk) items, fixed for the task's passes
+            int it_q[kMaxItems], it_v[kMaxItems];
+            int nit = 0;
+#pragma unroll
+            for (int n = 0; n < kMaxItems; ++n) {
+                const int item = warp + n * NCW;
+                it_q[n] = it_v[n] = 0;
+                if (item < U * nwc) {
+                    const int j = item / nwc, k = item - j * nwc;
+                    const int v = k * wpw + wl;
+                    it_v[n] = v;
+                    // offset of the column in the stage (pass-relative) and in xs at b = 0
+                    it_q[n] = j * L * pitch + v * L + col;
+                    nit = n + 1;
+                }
+            }
+            for (int b = 0; b < L; ++b) {
+                bool bad = !mbar_wait_timed(A, &full[s_cur], (fph >> s_cur) & 1u);
+                fph ^= 1u << s_cur;
+                float *stg = stage0 + (size_t)s_cur * A.stage_floats;
+                const int nv = b <= rem0 ? nv0 : nv0 - 1;
+#pragma unroll
+                for (int n = 0; n < kMaxItems; ++n) {
+                    if (n >= nit) break;
+                    const bool on = lane_on && it_v[n] < nv;
+                    float *xr = xs + it_q[n] + b;
+                    float *qr = stg + it_q[n];
+                    float y[LB];
+                    float sq = 0.f;
+                    if (on) {
+#pragma unroll
+                        for (int i = 0; i < LB; ++i)
+                            if (i < L) {
+                                y[i] = xr[i * pitch] + (first ? 0.f : qr[i * pitch]);
+                                sq = fmaf(y[i], y[i], sq);
+                            }
+                    }
+                    // window sum over its L lanes, in column order
+                    const int base = wl * L;
+                    float cs[LB];
+#pragma unroll
+                    for (int m = 0; m < LB; ++m)
+                        cs[m] = m < L ? __shfl_sync(0xffffffffu, sq, (base + m) & 31) : 0.f;
+                    float t = 0.f;
+#pragma unroll
+                    for (int m = 0; m < LB; ++m)
+                        if (m < L) t += cs[m];
+                    float scale = 1.f;
+                    const bool near = on && fabsf(t - ts.cS) <= kNearBand * ts.cS;
+                    if (on && t > ts.cS) scale = ts.sqrt_cS * rsqrtf(t);
+                    if (__any_sync(0xffffffffu, near)) {
+                        // rare: redo the sums of windows near the boundary in FP64
+                        double sq64 = 0.0;
+                        if (on) {
+#pragma unroll
+                            for (int i = 0; i < LB; ++i)
+                                if (i < L) sq64 = fma((double)y[i], (double)y[i], sq64);
+                        }
+                        double t64 = 0.0;
+#pragma unroll
+                        for (int m = 0; m < LB; ++m) {
+                            const double v64 = __shfl_sync(0xffffffffu, sq64, (base + m) & 31);
+                            if (m < L) t64 += v64;
+                        }
+                        if (near) scale = t64 > ts.cS64 ? (float)sqrt(ts.cS64 / t64) : 1.f;
+                    }
+                    if (on) {
+#pragma unroll
+                        for (int i = 0; i < LB; ++i)
+                            if (i < L) {
+                                const float xn = y[i] * scale;
+                                xr[i * pitch] = xn;
+                                qr[i * pitch] = y[i] - xn;
+                            }
+                    }
+                }
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&written[s_cur]);
+                s_cur = s_cur + 1 == S ? 0 : s_cur + 1;
+                if (consumers_sync_or(bad, NC)) {   // also orders xs between passes
+                    aborted = true;
+                    break;
+                }
+            }
+            if (aborted) break;
+
+            // x back to L2; fused cycle norm on the rows this task touches last
+            {
+                const int n4 = rows * pitch / 4;
+                const int q4 = pitch / 4;
+                float4 *dst = reinterpret_cast<float4 *>(A.x + (size_t)ts.r_first * pitch);
+                const float4 *src = reinterpret_cast<const float4 *>(xs);
+                for (int i = tid; i < n4; i += NC) {
+                    const float4 v = src[i];
+                    dst[i] = v;
+                    const int rr = i / q4;
+                    const int c4 = (i - rr * q4) * 4;
+                    if (((ts.final_mask >> rr) & 1ull) && c4 < A.W) {
+                        float4 *pp = reinterpret_cast<float4 *>(A.xprev + (size_t)(ts.r_first + rr) * pitch) + (i - rr * q4);
+                        const float4 pv = __ldcg(pp);
+                        const float xv[4] = {v.x, v.y, v.z, v.w};
+                        const float pw[4] = {pv.x, pv.y, pv.z, pv.w};
+#pragma unroll
+                        for (int e = 0; e < 4; ++e)
+                            if (c4 + e < A.W) {
+                                const double dd = (double)xv[e] - (double)pw[e];
+                                d2 = fma(dd, dd, d2);
+                                n2 = fma((double)pw[e], (double)pw[e], n2);
+                            }
+                        *pp = v;
+                    }
+                }
+            }
+            consumers_sync(NC);
+            if (tid == 0) {
+                __threadfence();
+                st_release(A.flags + ts.gid, (unsigned)(cyc + 1));
+            }
+        }
+
+        // ---- end of cycle: publish norms, grid barrier, same decision everywhere
+        int dec = kGo;
+        double step = 0.0, prev = 0.0;
+        if (aborted) {
+            dec = kAbort;
+        } else {
+            double *slot = A.partials + (size_t)(cyc & 1) * 2 * G;   // double-buffered
+            double a = d2, bb = n2;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                a += __shfl_xor_sync(0xffffffffu, a, o);
+                bb += __shfl_xor_sync(0xffffffffu, bb, o);
+            }
+            if (lane == 0) {
+                s_red[0][warp] = a;
+                s_red[1][warp] = bb;
+            }
+            consumers_sync(NC);
+            if (tid == 0) {
+                double D = 0.0, N = 0.0;
+                for (int w = 0; w < NCW; ++w) {
+                    D += s_red[0][w];
+                    N += s_red[1][w];
+                }
+                slot[2 * (size_t)cta] = D;
+                slot[2 * (size_t)cta + 1] = N;
+                __threadfence();
+                atomicAdd(A.barrier, 1u);
+                s_abort = wait_geq(A, A.barrier, (unsigned)G * (unsigned)(cyc + 1)) ? 0 : 1;
+            }
+            consumers_sync(NC);
+            d2 = 0.0;
+            n2 = 0.0;
+            if (s_abort) {
+                dec = kAbort;
+            } else {
+                // every CTA sums the partials in the same fixed tree, in parallel:
+                // thread i loads partial i, warps reduce by xor butterfly, then
+                // the warp sums are added in warp order
+                double a = 0.0, bq = 0.0;
+                for (int i = tid; i < G; i += NC) {
+                    a += __ldcg(slot + 2 * (size_t)i);
+                    bq += __ldcg(slot + 2 * (size_t)i + 1);
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    a += __shfl_xor_sync(0xffffffffu, a, o);
+                    bq += __shfl_xor_sync(0xffffffffu, bq, o);
+                }
+                if (lane == 0) {
+                    s_red[0][warp] = a;
+                    s_red[1][warp] = bq;
+                }
+                consumers_sync(NC);
+                double D = 0.0, N = 0.0;
+                for (int w = 0; w < NCW; ++w) {
+                    D += s_red[0][w];
+                    N += s_red[1][w];
+                }
+                step = sqrt(D);
+                prev = sqrt(N);
+                const bool conv = A.tol >= 0.0 && (A.tol_relative ? step <= A.tol * prev : step <= A.tol);
+                const bool cap = cyc + 1 >= A.max_cycles;
+                dec = (conv || cap) ? kStop : kGo;
+                if (cta == 0 && tid == 0) {
+                    if (cyc < A.hist_cap) {
+                        A.hist[2 * cyc] = step;
+                        A.hist[2 * cyc + 1] = prev;
+                    }
+                    A.ctl->cycles = cyc + 1;
+                    A.ctl->step = step;
+                    A.ctl->prev_norm = prev;
+                    if (dec == kStop) {
+                        A.ctl->stop = 1;
+                        if (!conv && A.tol >= 0.0)
+                            atomicCAS(&A.ctl->status, (int)SMRE_OK, (int)SMRE_ENOTCONVERGED);
+                    }
+                }
+            }
+        }
+        if (tid == 0) s_dec = dec;
+        cta_sync_all();
+        cta_sync_all();
+        if (dec != kGo) break;
+    }
+}
+
+template <int LB>
+cudaError_t launch_persist_t(const PersistArgs &A, int grid, int threads, size_t smem,
+                             cudaStream_t s)
+{
+    auto k = persist_kernel<LB>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    void *args[] = {const_cast<PersistArgs *>(&A)};
+    return cudaLaunchCooperativeKernel((const void *)k, dim3(grid), dim3(threads), args, smem, s);
+}
+
+const void *pick_kernel(int LB)
+{
+    if (LB <= 4) return (const void *)persist_kernel<4>;
+    if (LB <= 8) return (const void *)persist_kernel<8>;
+    if (LB <= 16) return (const void *)persist_kernel<16>;
+    if (LB <= 32) return (const void *)persist_kernel<32>;
+    return nullptr;
+}
+
+}  // namespace
+
+bool persist_supported(int max_side) { return pick_kernel(max_side) != nullptr; }
+
+cudaError_t persist_occupancy(int max_side, int threads, size_t smem, int *blocks_per_sm)
+{
+    const void *k = pick_kernel(max_side);
+    if (!k) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, threads, smem);
+}
+
+cudaError_t launch_persist(const PersistArgs &A, int max_side, int grid, int threads, size_t smem,
+                           cudaStream_t s)
+{
+    if (max_side <= 4) return launch_persist_t<4>(A, grid, threads, smem, s);
+    if (max_side <= 8) return launch_persist_t<8>(A, grid, threads, smem, s);
+    if (max_side <= 16) return launch_persist_t<16>(A, grid, threads, smem, s);
+    if (max_side <= 32) return launch_persist_t<32>(A, grid, threads, smem, s);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace smre

@@ -34,16 +34,23 @@ def err(a, ref):
     return float(np.abs(np.asarray(a, np.float64) - ref).max() / max(np.abs(ref).max(), 1e-300))
 
 
-def run_std(smre, torch, x0, sides, cS, max_cycles, tol=-1.0, rel=False, flags=0, stream=None):
+def run_std(smre, torch, x0, sides, cS, max_cycles, tol=-1.0, rel=False, flags=0, stream=None,
+            want_launches=False):
     H, W = x0.shape
     with smre.Projector(H, W, sides, stream=stream, cmode=smre.SMRE_C_EXPLICIT,
                         c_explicit=list(cS), max_cycles=max_cycles, tol=tol, tol_relative=rel,
                         flags=flags) as P:
         xd = torch.from_numpy(np.ascontiguousarray(x0, np.float32)).cuda()
         out = torch.empty_like(xd)
+        l0 = P.kernel_launches()
         res = P.project(xd, out)
         hist = P.history()
+        if want_launches:
+            return out.cpu().numpy(), res, hist, P.kernel_launches() - l0
         return out.cpu().numpy(), res, hist
+
+
+PATHS = {"persistent": 0, "group": 2}   # 2 = SMRE_F_GROUP_LAUNCHES
 
 
 def f32(x):
@@ -61,17 +68,53 @@ def f32(x):
     (5, 1029, [1, 2, 3, 4, 5]),      # two columns per thread, ragged tail
     (9, 2500, [2, 9]),               # four columns per thread
 ])
-def test_one_and_three_cycles_match_oracle(smre, torch_cuda, oracle_mod, H, W, sides):
+@pytest.mark.parametrize("path", list(PATHS))
+def test_one_and_three_cycles_match_oracle(smre, torch_cuda, oracle_mod, H, W, sides, path):
     from synthetic import blobs_residual
     x0 = f32(blobs_residual(H, W, n_blobs=max(1, H * W // 800), seed=H * 1000 + W))
     cS = oracle_mod.bounds(sides, 0.9)
     for cyc in (1, 3):
-        got, res, hist = run_std(smre, torch_cuda, x0, sides, cS, cyc)
+        got, res, hist = run_std(smre, torch_cuda, x0, sides, cS, cyc, flags=PATHS[path])
         ref = oracle_mod.dykstra(x0.astype(np.float64), sides, cS, max_cycles=cyc, tol=-1,
                                  n_threads=NTH)
         assert res.cycles == cyc
         assert err(got, ref.x) <= TOL, err(got, ref.x)
         assert np.allclose(hist, ref.hist, rtol=1e-4, atol=1e-6 * np.abs(ref.hist).max())
+
+
+@pytest.mark.parametrize("H,W,sides", [(64, 64, [1, 2, 4]), (512, 512, list(range(1, 9))),
+                                       (37, 53, [1, 2, 3, 5]), (200, 700, [1, 3, 6, 7])])
+def test_persistent_and_group_paths_agree_bitwise(smre, torch_cuda, oracle_mod, H, W, sides):
+    """Both schedules run the same per-window arithmetic in the same set order."""
+    from synthetic import emitter_residual
+    x0 = f32(emitter_residual(H, W, n_emitters=max(1, H * W // 600), seed=H + W))
+    cS = oracle_mod.bounds(sides, 0.9)
+    a, ra, ha, la = run_std(smre, torch_cuda, x0, sides, cS, 5, want_launches=True)
+    b, rb, hb, lb = run_std(smre, torch_cuda, x0, sides, cS, 5, flags=PATHS["group"],
+                            want_launches=True)
+    assert la == 1, la                      # one cooperative launch for all cycles
+    assert lb > 5 * len(set(sides))
+    assert np.array_equal(a, b)
+    assert np.allclose(ha, hb, rtol=1e-12)
+
+
+def test_persistent_timeout_is_reported_and_handle_survives(smre, torch_cuda, oracle_mod):
+    """A device-side wait on a flag nothing sets runs out after 50 ms; the call
+    returns ETIMEOUT and the same handle then projects normally."""
+    sides = [1, 2, 3]
+    x0 = f32(np.random.default_rng(9).standard_normal((96, 80)) * 3)
+    cS = oracle_mod.bounds(sides, 0.9)
+    with smre.Projector(96, 80, sides, cmode=smre.SMRE_C_EXPLICIT, c_explicit=list(cS),
+                        max_cycles=4, flags=4) as P:          # 4 = SMRE_F_SELFTEST_TIMEOUT
+        xd = torch_cuda.from_numpy(x0).cuda()
+        out = torch_cuda.empty_like(xd)
+        with pytest.raises(smre.SmreError) as ei:
+            P.project(xd, out)
+        assert ei.value.status == smre.SMRE_ETIMEOUT
+        torch_cuda.cuda.synchronize()          # the context is still healthy
+    got, res, _ = run_std(smre, torch_cuda, x0, sides, cS, 4)
+    ref = oracle_mod.dykstra(x0.astype(np.float64), sides, cS, max_cycles=4, tol=-1)
+    assert err(got, ref.x) <= TOL
 
 
 def test_window_count_reported(smre, torch_cuda, oracle_mod):
