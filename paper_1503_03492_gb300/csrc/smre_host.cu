@@ -68,6 +68,7 @@ struct smre_dykstra {
     int p_sched_bytes = 0;
     unsigned *d_flags = nullptr, *d_barrier = nullptr, *d_selftest = nullptr;
     double *d_ppartials = nullptr;
+    float *d_zeros = nullptr;
     int *d_abort = nullptr;
     unsigned long long timeout_ns = 10000000000ull;
     std::string err;
@@ -363,6 +364,7 @@ smre_status plan_persistent(smre_dykstra *h, int flags)
     std::vector<unsigned char> sched;
     std::vector<int4> cta_sched(G);
     int maxL = 0, max_items = 1;
+    double items_ratio = 0.0;   // max over tasks of items / items allowed per warp
     long long stage_floats = 0;
     size_t seg_max = 16;
     size_t i = 0;
@@ -393,7 +395,9 @@ smre_status plan_persistent(smre_dykstra *h, int flags)
             maxL = std::max(maxL, t.L);
             {
                 const int wpw = 32 / t.L, nv = W / t.L;
-                max_items = std::max(max_items, t.U * ((nv + wpw - 1) / wpw));
+                const int items = t.U * ((nv + wpw - 1) / wpw);
+                max_items = std::max(max_items, items);
+                items_ratio = std::max(items_ratio, (double)items / max_items_for_side(t.L));
             }
             stage_floats = std::max(stage_floats, (long long)t.U * t.L * pitch);
             if (t.U * t.L > 64) return SMRE_OK;   // row mask would not fit
@@ -416,7 +420,7 @@ smre_status plan_persistent(smre_dykstra *h, int flags)
 
     if (!persist_supported(maxL)) return SMRE_OK;
     const int ncw = std::max(4, std::min(kPersistThreads / 32 - 1, max_items));
-    if (max_items > kMaxItems * ncw) return SMRE_OK;   // too many items per warp
+    if (items_ratio > ncw) return SMRE_OK;   // too many items per warp
     const int threads = (ncw + 1) * 32;
     const size_t xs_bytes = (size_t)stage_floats * 4;   // the largest task's rows
     const size_t stage_offset = 512 + (seg_max + 127) / 128 * 128;
@@ -424,7 +428,9 @@ smre_status plan_persistent(smre_dykstra *h, int flags)
     if (budget < stage_offset + xs_bytes) return SMRE_OK;
     const long long fit = (long long)((budget - stage_offset - xs_bytes) / (stage_floats * 4));
     const int S = (int)std::min<long long>(kMaxStages, fit);
-    if (S < 3) return SMRE_OK;
+    // warps without windows may run up to L passes ahead within a task, so
+    // the ring must hold more passes than the longest task
+    if (S < 3 || S <= maxL) return SMRE_OK;
     const size_t smem = stage_offset + (size_t)S * stage_floats * 4 + xs_bytes;
     int occ = 0;
     cudaError_t oe = persist_occupancy(maxL, threads, smem, &occ);
@@ -449,6 +455,9 @@ smre_status plan_persistent(smre_dykstra *h, int flags)
     CK(h, cudaMemset(h->d_selftest, 0, 64));
     CK(h, cudaMalloc(&h->d_abort, 64));
     CK(h, cudaMalloc(&h->d_ppartials, sizeof(double) * 4 * G));
+    CK(h, cudaMalloc(&h->d_zeros, sizeof(float) * stage_floats));
+    CK(h, cudaMemset(h->d_zeros, 0, sizeof(float) * stage_floats));
+    h->dev_bytes += sizeof(float) * stage_floats;
     h->dev_bytes += sizeof(unsigned) * tasks.size() + 192 + sizeof(double) * 4 * G;
     h->n_tasks = (int)tasks.size();
     h->p_grid = G;
@@ -477,6 +486,7 @@ smre_status run_persistent(smre_dykstra *h)
     A.x = h->xw;
     A.xprev = h->xprev;
     A.q = h->q;
+    A.zeros = h->d_zeros;
     A.pitch = h->pitch;
     A.H = h->H;
     A.W = h->W;
@@ -863,6 +873,7 @@ void smre_dykstra_destroy(smre_dykstra *h)
     cudaFree(h->d_selftest);
     cudaFree(h->d_abort);
     cudaFree(h->d_ppartials);
+    cudaFree(h->d_zeros);
     if (h->ctl_host) cudaFreeHost(h->ctl_host);
     if (h->viol_host) cudaFreeHost(h->viol_host);
     if (h->ev0) cudaEventDestroy(h->ev0);

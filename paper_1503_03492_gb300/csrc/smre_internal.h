@@ -58,8 +58,10 @@ struct GroupArgs {
 // ---- persistent standard path (smre_persist.cu)
 
 constexpr int kMaxStages = 16;    // ring stages of the increment stream
-constexpr int kPersistThreads = 640;   // most threads per CTA of the persistent kernel
+constexpr int kPersistThreads = 576;   // most threads per CTA of the persistent kernel
 constexpr int kMaxItems = 4;          // (unit, window chunk) items per consumer warp and task
+// items a consumer warp may hold in one task of side L (register budget)
+__host__ __device__ constexpr int max_items_for_side(int L) { return L <= 4 ? 4 : (L <= 8 ? 2 : 1); }
 
 // Task = the units of one group owned by one CTA (a contiguous row band).
 struct TaskDesc {
@@ -90,6 +92,7 @@ struct TaskS {
 
 struct PersistArgs {
     float *x, *xprev, *q;
+    const float *zeros;          // stage_floats zero floats (increments of the first cycle)
     int pitch, H, W;
     int consumer_warps;          // warps 0..consumer_warps-1 consume, the next one produces
     // per-CTA schedule: TaskS[n_tasks] | long long pass_qoff[n_passes] | int deps[n_deps]

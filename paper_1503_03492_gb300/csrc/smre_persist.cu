@@ -74,6 +74,22 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity)
     return ok != 0;
 }
 
+// The same test, but a thread whose phase is not complete is suspended by the
+// hardware (up to `ns` nanoseconds) instead of spinning, so waiting warps
+// leave the issue slots to the warps that work.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t *bar, unsigned parity, unsigned ns)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(ns)
+        : "memory");
+    return ok != 0;
+}
+
 __device__ __forceinline__ void bulk_load(void *dst_smem, const void *src, unsigned bytes,
                                           uint64_t *bar)
 {
@@ -141,13 +157,13 @@ __device__ bool wait_geq(const PersistArgs &A, const unsigned *p, unsigned targe
     const unsigned long long t0 = globaltimer();
     for (unsigned it = 0;; ++it) {
         if (ld_acquire(p) >= target) return true;
-        if ((it & 63) == 63) {
+        if (it >= 4) __nanosleep(40);
+        if ((it & 31) == 31) {
             if (ld_volatile(A.abort_word)) return false;
             if (globaltimer() - t0 > A.timeout_ns) {
                 raise_timeout(A);
                 return false;
             }
-            __nanosleep(64);
         }
     }
 }
@@ -158,14 +174,12 @@ __device__ bool mbar_wait_timed(const PersistArgs &A, uint64_t *bar, unsigned pa
 {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = globaltimer();
-    for (unsigned it = 0;; ++it) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 255) == 255) {
-            if (ld_volatile(A.abort_word)) return false;
-            if (globaltimer() - t0 > A.timeout_ns) {
-                raise_timeout(A);
-                return false;
-            }
+    for (;;) {
+        if (mbar_try_wait_sleep(bar, parity, 20000u)) return true;
+        if (ld_volatile(A.abort_word)) return false;
+        if (globaltimer() - t0 > A.timeout_ns) {
+            raise_timeout(A);
+            return false;
         }
     }
 }
@@ -202,6 +216,136 @@ __device__ __forceinline__ void consumers_sync(int nthreads)
 
 __device__ __forceinline__ void cta_sync_all() { asm volatile("barrier.sync 0;" ::: "memory"); }
 
+// named barrier 2 among the warps that hold windows in the current task
+__device__ __forceinline__ void workers_sync(int nthreads)
+{
+    if (nthreads == 32) __syncwarp();
+    else asm volatile("barrier.sync 2, %0;" ::"r"(nthreads) : "memory");
+}
+
+// Everything a consumer warp needs to run the passes of one task.
+struct PassCtx {
+    const PersistArgs *A;
+    uint64_t *full, *written;
+    float *stage0, *xs;
+    volatile int *pass_abort;   // shared: set by a worker whose copy did not arrive
+    int S, NCW, NC, warp, lane, pitch;
+};
+
+// The L passes b = 0..L-1 of one task, side L known at compile time.  Returns
+// true when the launch must be abandoned (a copy did not arrive in time).
+template <int L>
+__device__ __forceinline__ bool run_passes(const PassCtx &cx, const TaskS &ts, int &s_cur,
+                                           unsigned &fph)
+{
+    constexpr int wpw = 32 / L;                     // windows per warp
+    constexpr int MI = max_items_for_side(L);       // items per warp and task
+    const int lane = cx.lane, warp = cx.warp, pitch = cx.pitch;
+    const int wl = lane / L, col = lane - wl * L;   // window of the lane, column in it
+    const int base = wl * L;
+    const bool lane_on = lane < wpw * L;
+    const int W = cx.A->W, U = ts.U;
+    const int nv0 = W / L, rem0 = W - nv0 * L;      // pass b has nv0 - (b > rem0) windows
+    const int nwc = (nv0 + wpw - 1) / wpw;          // warp chunks per unit
+    // this warp's (unit, chunk) items, fixed for the task's passes
+    int it_q[MI], it_v[MI];
+    int nit = 0;
+#pragma unroll
+    for (int n = 0; n < MI; ++n) {
+        const int item = warp + n * cx.NCW;
+        it_q[n] = 0;
+        it_v[n] = 1 << 30;
+        if (item < U * nwc) {
+            const int j = item / nwc, k = item - j * nwc;
+            it_v[n] = k * wpw + wl;
+            it_q[n] = j * L * pitch + it_v[n] * L + col;   // column offset (pass-relative)
+            nit = n + 1;
+        }
+    }
+    const int nwork = U * nwc < cx.NCW ? U * nwc : cx.NCW;   // warps holding items
+    if (nit == 0) {
+        // no window of this task in this warp: release every pass's stage at
+        // once (the increments are untouched here) and wait at the task end
+        for (int b = 0; b < L; ++b) {
+            fph ^= 1u << s_cur;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&cx.written[s_cur]);
+            s_cur = s_cur + 1 == cx.S ? 0 : s_cur + 1;
+        }
+        return false;
+    }
+    const float cS = ts.cS, sqrt_cS = ts.sqrt_cS;
+    for (int b = 0; b < L; ++b) {
+        const int s = s_cur;
+        const bool bad = !mbar_wait_timed(*cx.A, &cx.full[s], (fph >> s) & 1u);
+        fph ^= 1u << s;
+        float *stg = cx.stage0 + (size_t)s * cx.A->stage_floats;
+        const int nv = b <= rem0 ? nv0 : nv0 - 1;
+#pragma unroll
+        for (int n = 0; n < MI; ++n) {
+            if (n >= nit) break;
+            const bool on = lane_on && it_v[n] < nv;
+            float *xr = cx.xs + it_q[n] + b;
+            float *qr = stg + it_q[n];
+            float y[L];
+            float sq = 0.f;
+            if (on) {
+#pragma unroll
+                for (int i = 0; i < L; ++i) y[i] = xr[i * pitch] + qr[i * pitch];
+#pragma unroll
+                for (int i = 0; i < L; ++i) sq = fmaf(y[i], y[i], sq);
+            }
+            // window sum over its L lanes, in column order
+            float t = 0.f;
+#pragma unroll
+            for (int m = 0; m < L; ++m) t += __shfl_sync(0xffffffffu, sq, (base + m) & 31);
+            float scale = 1.f;
+            const bool near = on && fabsf(t - cS) <= kNearBand * cS;
+            if (on && t > cS) scale = sqrt_cS * rsqrtf(t);
+            if (__any_sync(0xffffffffu, near)) {
+                // rare: redo the sums of windows near the boundary in FP64
+                double sq64 = 0.0;
+                if (on) {
+#pragma unroll
+                    for (int i = 0; i < L; ++i) sq64 = fma((double)y[i], (double)y[i], sq64);
+                }
+                double t64 = 0.0;
+#pragma unroll
+                for (int m = 0; m < L; ++m) t64 += __shfl_sync(0xffffffffu, sq64, (base + m) & 31);
+                if (near) scale = t64 > ts.cS64 ? (float)sqrt(ts.cS64 / t64) : 1.f;
+            }
+            if (on) {
+#pragma unroll
+                for (int i = 0; i < L; ++i) {
+                    const float xn = y[i] * scale;
+                    xr[i * pitch] = xn;
+                    qr[i * pitch] = y[i] - xn;
+                }
+            }
+        }
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&cx.written[s]);
+        s_cur = s + 1 == cx.S ? 0 : s + 1;
+        if (bad) *cx.pass_abort = 1;
+        workers_sync(nwork * 32);                         // orders xs between passes
+        if (*cx.pass_abort) return true;                  // copies lost: abandon (uniformly)
+    }
+    return false;
+}
+
+__device__ __forceinline__ bool run_task_passes(const PassCtx &cx, const TaskS &ts, int &s_cur,
+                                             unsigned &fph)
+{
+    switch (ts.L) {
+#define RP(l) case l: return run_passes<l>(cx, ts, s_cur, fph);
+        RP(1) RP(2) RP(3) RP(4) RP(5) RP(6) RP(7) RP(8)
+        RP(9) RP(10) RP(11) RP(12) RP(13) RP(14) RP(15) RP(16)
+#undef RP
+        default: return true;
+    }
+}
+
 enum { kGo = 0, kStop = 1, kAbort = 2 };
 
 // ------------------------------------------------------------------ kernel
@@ -219,7 +363,6 @@ enum { kGo = 0, kStop = 1, kAbort = 2 };
 // k * wpw + l / L of its warp's chunk k; a window's column sums meet by
 // shuffles in a fixed order, so every lane of a window sees the same sum.
 // x of the task's rows lives in shared memory for the task's L passes.
-template <int LB>
 __global__ void __launch_bounds__(kPersistThreads, 1) persist_kernel(const PersistArgs A)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -231,6 +374,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1) persist_kernel(const Persi
     float *stage0 = reinterpret_cast<float *>(smem + A.stage_offset); // [S][stage_floats]
     float *xs = stage0 + (size_t)S * A.stage_floats;                  // [rows][pitch]
     __shared__ int s_dec, s_abort;
+    __shared__ volatile int s_pass_abort;
     __shared__ double s_red[2][32];
 
     const int tid = threadIdx.x;
@@ -261,6 +405,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1) persist_kernel(const Persi
         fence_mbar_init();
         s_dec = kGo;
         s_abort = 0;
+        s_pass_abort = 0;
     }
     __syncthreads();
 
@@ -274,18 +419,15 @@ __global__ void __launch_bounds__(kPersistThreads, 1) persist_kernel(const Persi
             if (lane == 0 && npass > 0 && !dead) {
                 auto provide = [&](int task, int b, int stg) {
                     s_prov[stg] += 1;
-                    if (first) {
-                        mbar_arrive(&full[stg]);
-                        return;
-                    }
                     const TaskS &ts = tasks_s[task];
                     const unsigned unit_bytes = (unsigned)(ts.L * pitch * sizeof(float));
                     mbar_arrive_expect_tx(&full[stg], unit_bytes * ts.U);
-                    const float *src = A.q + pass_qoff[ts.pass0 + b];
+                    // the first cycle starts from q = 0: copy from a zeroed block
+                    const float *src = first ? A.zeros : A.q + pass_qoff[ts.pass0 + b];
                     float *dst = stage0 + (size_t)stg * A.stage_floats;
                     for (int j = 0; j < ts.U; ++j)
-                        bulk_load(dst + (size_t)j * ts.L * pitch, src + (size_t)j * ts.L * pitch,
-                                  unit_bytes, &full[stg]);
+                        bulk_load(dst + (size_t)j * ts.L * pitch,
+                                  first ? src : src + (size_t)j * ts.L * pitch, unit_bytes, &full[stg]);
                 };
                 int rt = 0, rb = 0, rs = s_head;       // refill cursor
                 const int pre = npass < S ? npass : S;
@@ -339,6 +481,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1) persist_kernel(const Persi
     }
 
     // ======================================================== consumer warps
+    const PassCtx cx{&A, full, written, stage0, xs, &s_pass_abort, S, NCW, NC, warp, lane, pitch};
     int s_cur = 0;
     unsigned fph = 0;            // parity of the next `full` wait, per stage
     double d2 = 0.0, n2 = 0.0;   // this thread's share of the cycle norm
@@ -372,95 +515,9 @@ __global__ void __launch_bounds__(kPersistThreads, 1) persist_kernel(const Persi
             }
             consumers_sync(NC);
 
-            const int wpw = 32 / L;                  // windows per warp
-            const int wl = lane / L, col = lane - wl * L;   // window of the lane, column in it
-            const bool lane_on = lane < wpw * L;
-            const int nv0 = A.W / L, rem0 = A.W - nv0 * L;  // windows of pass b: nv0 - (b > rem0)
-            const int nwc = (nv0 + wpw - 1) / wpw;          // warp chunks per unit
-            // this warp's (unit, chunk) items, fixed for the task's passes
-            int it_q[kMaxItems], it_v[kMaxItems];
-            int nit = 0;
-#pragma unroll
-            for (int n = 0; n < kMaxItems; ++n) {
-                const int item = warp + n * NCW;
-                it_q[n] = it_v[n] = 0;
-                if (item < U * nwc) {
-                    const int j = item / nwc, k = item - j * nwc;
-                    const int v = k * wpw + wl;
-                    it_v[n] = v;
-                    // offset of the column in the stage (pass-relative) and in xs at b = 0
-                    it_q[n] = j * L * pitch + v * L + col;
-                    nit = n + 1;
-                }
-            }
-            for (int b = 0; b < L; ++b) {
-                bool bad = !mbar_wait_timed(A, &full[s_cur], (fph >> s_cur) & 1u);
-                fph ^= 1u << s_cur;
-                float *stg = stage0 + (size_t)s_cur * A.stage_floats;
-                const int nv = b <= rem0 ? nv0 : nv0 - 1;
-#pragma unroll
-                for (int n = 0; n < kMaxItems; ++n) {
-                    if (n >= nit) break;
-                    const bool on = lane_on && it_v[n] < nv;
-                    float *xr = xs + it_q[n] + b;
-                    float *qr = stg + it_q[n];
-                    float y[LB];
-                    float sq = 0.f;
-                    if (on) {
-#pragma unroll
-                        for (int i = 0; i < LB; ++i)
-                            if (i < L) {
-                                y[i] = xr[i * pitch] + (first ? 0.f : qr[i * pitch]);
-                                sq = fmaf(y[i], y[i], sq);
-                            }
-                    }
-                    // window sum over its L lanes, in column order
-                    const int base = wl * L;
-                    float cs[LB];
-#pragma unroll
-                    for (int m = 0; m < LB; ++m)
-                        cs[m] = m < L ? __shfl_sync(0xffffffffu, sq, (base + m) & 31) : 0.f;
-                    float t = 0.f;
-#pragma unroll
-                    for (int m = 0; m < LB; ++m)
-                        if (m < L) t += cs[m];
-                    float scale = 1.f;
-                    const bool near = on && fabsf(t - ts.cS) <= kNearBand * ts.cS;
-                    if (on && t > ts.cS) scale = ts.sqrt_cS * rsqrtf(t);
-                    if (__any_sync(0xffffffffu, near)) {
-                        // rare: redo the sums of windows near the boundary in FP64
-                        double sq64 = 0.0;
-                        if (on) {
-#pragma unroll
-                            for (int i = 0; i < LB; ++i)
-                                if (i < L) sq64 = fma((double)y[i], (double)y[i], sq64);
-                        }
-                        double t64 = 0.0;
-#pragma unroll
-                        for (int m = 0; m < LB; ++m) {
-                            const double v64 = __shfl_sync(0xffffffffu, sq64, (base + m) & 31);
-                            if (m < L) t64 += v64;
-                        }
-                        if (near) scale = t64 > ts.cS64 ? (float)sqrt(ts.cS64 / t64) : 1.f;
-                    }
-                    if (on) {
-#pragma unroll
-                        for (int i = 0; i < LB; ++i)
-                            if (i < L) {
-                                const float xn = y[i] * scale;
-                                xr[i * pitch] = xn;
-                                qr[i * pitch] = y[i] - xn;
-                            }
-                    }
-                }
-                fence_proxy_async_smem();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&written[s_cur]);
-                s_cur = s_cur + 1 == S ? 0 : s_cur + 1;
-                if (consumers_sync_or(bad, NC)) {   // also orders xs between passes
-                    aborted = true;
-                    break;
-                }
+            {
+                const bool ab = run_task_passes(cx, ts, s_cur, fph);
+                if (consumers_sync_or(ab, NC)) aborted = true;   // xs complete for the store
             }
             if (aborted) break;
 
@@ -585,34 +642,24 @@ __global__ void __launch_bounds__(kPersistThreads, 1) persist_kernel(const Persi
     }
 }
 
-template <int LB>
 cudaError_t launch_persist_t(const PersistArgs &A, int grid, int threads, size_t smem,
                              cudaStream_t s)
 {
-    auto k = persist_kernel<LB>;
+    auto k = persist_kernel;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     void *args[] = {const_cast<PersistArgs *>(&A)};
     return cudaLaunchCooperativeKernel((const void *)k, dim3(grid), dim3(threads), args, smem, s);
 }
 
-const void *pick_kernel(int LB)
-{
-    if (LB <= 4) return (const void *)persist_kernel<4>;
-    if (LB <= 8) return (const void *)persist_kernel<8>;
-    if (LB <= 16) return (const void *)persist_kernel<16>;
-    if (LB <= 32) return (const void *)persist_kernel<32>;
-    return nullptr;
-}
-
 }  // namespace
 
-bool persist_supported(int max_side) { return pick_kernel(max_side) != nullptr; }
+bool persist_supported(int max_side) { return max_side >= 1 && max_side <= 16; }
 
 cudaError_t persist_occupancy(int max_side, int threads, size_t smem, int *blocks_per_sm)
 {
-    const void *k = pick_kernel(max_side);
-    if (!k) return cudaErrorInvalidValue;
+    (void)max_side;
+    const void *k = (const void *)persist_kernel;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, threads, smem);
@@ -621,11 +668,8 @@ cudaError_t persist_occupancy(int max_side, int threads, size_t smem, int *block
 cudaError_t launch_persist(const PersistArgs &A, int max_side, int grid, int threads, size_t smem,
                            cudaStream_t s)
 {
-    if (max_side <= 4) return launch_persist_t<4>(A, grid, threads, smem, s);
-    if (max_side <= 8) return launch_persist_t<8>(A, grid, threads, smem, s);
-    if (max_side <= 16) return launch_persist_t<16>(A, grid, threads, smem, s);
-    if (max_side <= 32) return launch_persist_t<32>(A, grid, threads, smem, s);
-    return cudaErrorInvalidValue;
+    (void)max_side;
+    return launch_persist_t(A, grid, threads, smem, s);
 }
 
 }  // namespace smre
