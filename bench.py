@@ -120,6 +120,15 @@ class Clocks:
                 "power_w_max": pmax}
 
 
+# DRAM traffic of the dominant kernel from one ncu capture (20 cycles of this
+# workload, profiles/persist_kernel_emitters512_20cycles_full.md), per library
+# version: (first-cycle bytes, bytes per later cycle).  A version without an
+# entry reports traffic as null until it is captured again.
+MEASURED_TRAFFIC = {
+    "smre-gb300 0.2 (sm_103a)": (0.22e9, 424.0e6),
+}
+
+
 def measured_peak_hbm():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -277,13 +286,16 @@ def main():
     avg_std = sum(std_s) / len(std_s)
     achieved = (sum(std_bytes) / len(std_bytes)) / avg_std / 1e9
     clocks = clk.summary()
+    tr = MEASURED_TRAFFIC.get(smre.smre_version())
+    cyc_med = int(np.median(cycles))
+    traffic = None if tr is None else tr[0] + (cyc_med - 1) * tr[1]
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
         threads = os.cpu_count() or 1
-        cyc = 40
+        cyc = int(os.environ.get("SMRE_CPU_SAMPLE_CYCLES", "800"))
         wv, sv = cpu_sample(x0, threads, cyc)
         cpu = {"value": wv / sv, "unit": "window-projections/s", "cores": threads, "kind": "oracle",
                "sample": f"{cyc} of the {int(np.median(cycles))} standard cycles + the full "
@@ -304,8 +316,8 @@ def main():
                        "l2": "flushed between timed steps (256 MB write); q store 214 MB > L2",
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
-                         "kernel": "standard projection (all group launches of one call)",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "persist_kernel (one launch = one standard projection)",
                          "peak_source": peak_src,
                          "bytes_per_launch": sum(std_bytes) / len(std_bytes),
                          "seconds_per_launch": avg_std},

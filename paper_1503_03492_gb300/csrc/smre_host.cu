@@ -519,7 +519,7 @@ smre_status run_persistent(smre_dykstra *h)
 
 extern "C" {
 
-const char *smre_version(void) { return "smre-gb300 0.1 (sm_103a)"; }
+const char *smre_version(void) { return "smre-gb300 0.2 (sm_103a)"; }
 
 const char *smre_last_error(const smre_dykstra *h)
 {
