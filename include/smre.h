@@ -166,6 +166,36 @@ SMRE_API smre_status smre_dykstra_icd_sweeps(smre_dykstra *h, int *out, int n_ma
  * launch of every entry point; a monotone counter kept on the host). */
 SMRE_API long long smre_dykstra_kernel_launches(const smre_dykstra *h);
 
+/* Standard projection that allocates nothing (the paper has no counterpart:
+ * it is a service for callers of this library).  Some callers may not call
+ * cudaMalloc while they run -- a real-time acquisition pipeline that reserves
+ * all device memory when it starts, or a plugin whose host application's
+ * memory pool owns the device -- because the allocation can fail once the pool
+ * holds the memory, and it can synchronise the device in the middle of their
+ * time budget.  This entry point runs the same computation as
+ * smre_dykstra_create + smre_dykstra_project (with SMRE_F_GROUP_LAUNCHES) +
+ * smre_dykstra_destroy, but keeps every intermediate buffer (increments, work
+ * images, norms, control block, per-cycle history) in one static device array
+ * of 16 MiB inside the library, which every GPU that loads the library holds
+ * until the process exits.  It calls no cudaMalloc, cudaFree or other
+ * allocating routine.
+ *   p:    problem and stopping rule as for smre_dykstra_create (cmode PERSET,
+ *         CHI2 or EXPLICIT; MAXSTAT is rejected); p->flags is ignored.
+ *   cuda_stream: stream the work runs on (NULL: legacy default stream); the
+ *         call waits for it before returning.
+ *   x0, x: H x W float images (device or host), x may equal x0.
+ *   res:  optional host result, as for smre_dykstra_project.
+ * Sizes whose buffers exceed the 16 MiB array (roughly sum_L L^2 * H * W * 4
+ * bytes plus two images) are rejected with SMRE_EINVAL and a message naming
+ * the bytes needed.  The first call on each device looks up the array's
+ * device address (once per device, with that device current); make that first
+ * call before any stream capture begins.  All calls share the array and it
+ * keeps the last call's contents; calls whose work overlaps on the GPU (two
+ * streams, two threads) race and corrupt each other.
+ * Returns OK, ENOTCONVERGED (cap hit, x valid), EINVAL or ECUDA. */
+SMRE_API smre_status smre_dykstra_project_static(const smre_params *p, void *cuda_stream,
+                                                 const float *x0, float *x, smre_result *res);
+
 /* Bytes of device memory the handle holds. */
 SMRE_API size_t smre_dykstra_device_bytes(const smre_dykstra *h);
 

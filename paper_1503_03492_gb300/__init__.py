@@ -25,7 +25,7 @@ __all__ = [
     "smre_dykstra_project_incomplete", "smre_dykstra_set_stopping", "smre_dykstra_bounds",
     "smre_dykstra_history", "smre_dykstra_icd_sweeps", "smre_dykstra_device_bytes",
     "smre_dykstra_destroy", "smre_last_error", "smre_version", "Projector", "EXPORTED",
-    "smre_dykstra_kernel_launches", "make_params",
+    "smre_dykstra_kernel_launches", "make_params", "smre_dykstra_project_static",
 ]
 
 SMRE_OK, SMRE_EINVAL, SMRE_ENOMEM, SMRE_ECUDA, SMRE_ETIMEOUT, SMRE_ENOTCONVERGED = range(6)
@@ -42,6 +42,7 @@ EXPORTED = (
     "smre_dykstra_project_incomplete", "smre_dykstra_set_stopping", "smre_dykstra_bounds",
     "smre_dykstra_history", "smre_dykstra_icd_sweeps", "smre_dykstra_device_bytes",
     "smre_dykstra_destroy", "smre_last_error", "smre_version", "smre_dykstra_kernel_launches",
+    "smre_dykstra_project_static",
 )
 
 
@@ -109,6 +110,8 @@ def load():
         "smre_dykstra_icd_sweeps": (st, [H, P(ctypes.c_int), ctypes.c_int, P(ctypes.c_int)]),
         "smre_dykstra_device_bytes": (ctypes.c_size_t, [H]),
         "smre_dykstra_kernel_launches": (ctypes.c_longlong, [H]),
+        "smre_dykstra_project_static": (st, [P(smre_params), ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_void_p, P(smre_result)]),
         "smre_dykstra_destroy": (None, [H]),
         "smre_last_error": (ctypes.c_char_p, [H]),
         "smre_version": (ctypes.c_char_p, []),
@@ -252,6 +255,20 @@ def smre_dykstra_icd_sweeps(h):
 
 def smre_dykstra_device_bytes(h) -> int:
     return int(load().smre_dykstra_device_bytes(h))
+
+
+def smre_dykstra_project_static(params: smre_params, x0, x, stream=None, want_result=True):
+    """Standard projection without any device allocation (the library's static
+    16 MiB scratch holds every intermediate buffer); see include/smre.h."""
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    p0, k0 = _ptr(x0)
+    p1, k1 = _ptr(x)
+    res = smre_result()
+    st = load().smre_dykstra_project_static(ctypes.byref(params), ctypes.c_void_p(stream or 0),
+                                            p0, p1, ctypes.byref(res) if want_result else None)
+    _check(st, None, ok=(SMRE_OK, SMRE_ENOTCONVERGED))
+    return res if want_result else None
 
 
 def smre_dykstra_kernel_launches(h) -> int:

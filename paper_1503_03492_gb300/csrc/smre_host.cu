@@ -517,6 +517,10 @@ smre_status run_persistent(smre_dykstra *h)
 
 }  // namespace
 
+namespace smre {
+void set_thread_error(const char *msg) { g_err = msg; }
+}  // namespace smre
+
 extern "C" {
 
 const char *smre_version(void) { return "smre-gb300 0.2 (sm_103a)"; }

@@ -153,6 +153,9 @@ struct IcdArgs {
 };
 cudaError_t launch_icd_pass(const IcdArgs &a, cudaStream_t s);
 
+// Message returned by smre_last_error(NULL) on this thread (smre_host.cu).
+void set_thread_error(const char *msg);
+
 // Host FP64 helpers of Sec. 2.1 (smre_weights.cu).
 double inv_normal_cdf(double p);
 double chi2_quantile(double alpha, int k);

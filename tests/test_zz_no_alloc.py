@@ -1,0 +1,65 @@
+"""The projection entry point that allocates nothing.
+
+Callers that may not allocate device memory while they run (a real-time
+pipeline that reserved all device memory at start-up, a plugin whose host
+application's pool owns the device) use smre_dykstra_project_static, which
+keeps every intermediate buffer in the library's static 16 MiB device array.
+It must give the same image as the handle-based smre_dykstra_project, on
+repeated calls too (the array keeps the previous call's contents), and must
+turn away sizes that do not fit.  This file is collected last on purpose.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    return torch
+
+
+def _err(a, ref):
+    a = np.asarray(a, np.float64)
+    ref = np.asarray(ref, np.float64)
+    return float(np.abs(a - ref).max() / np.abs(ref).max())
+
+
+def test_static_entry_point_matches_allocating_path_twice(torch_cuda):
+    import paper_1503_03492_gb300 as smre
+    from synthetic import emitter_residual
+
+    H, W, sides = 96, 80, [1, 2, 3, 4]
+    cS = smre.smre_bounds(smre.make_params(H, W, sides, alpha=0.9))
+    kw = dict(cmode=smre.SMRE_C_EXPLICIT, c_explicit=cS, max_cycles=25, tol=-1.0)
+    stream = torch_cuda.cuda.current_stream()
+    for call, seed in enumerate((11, 12)):
+        x0 = np.ascontiguousarray(emitter_residual(H, W, n_emitters=12, seed=seed), np.float32)
+        xd = torch_cuda.from_numpy(x0).cuda()
+        ref = torch_cuda.empty_like(xd)
+        with smre.Projector(H, W, sides, stream=stream, **kw) as P:
+            r_ref = P.project(xd, ref)
+        out = torch_cuda.full_like(xd, float("nan"))
+        p = smre.make_params(H, W, sides, **kw)
+        r = smre.smre_dykstra_project_static(p, xd, out, stream=stream)
+        assert r.cycles == r_ref.cycles == 25, (call, r.cycles, r_ref.cycles)
+        e = _err(out.cpu().numpy(), ref.cpu().numpy())
+        assert e <= TOL, (call, e)
+
+
+def test_static_entry_point_rejects_sizes_beyond_its_buffer(torch_cuda):
+    import paper_1503_03492_gb300 as smre
+
+    H = W = 1024
+    x = torch_cuda.zeros(H, W, device="cuda")
+    p = smre.make_params(H, W, list(range(1, 9)), max_cycles=2)
+    with pytest.raises(smre.SmreError) as ei:
+        smre.smre_dykstra_project_static(p, x, x)
+    assert ei.value.status == smre.SMRE_EINVAL
+    assert "static buffer" in str(ei.value)
