@@ -61,7 +61,7 @@ struct smre_dykstra {
     bool persist = false;
     int p_grid = 0, p_threads = 0, p_stages = 0, p_ncw = 0, p_maxL = 0;
     size_t p_smem = 0;
-    int p_stage_floats = 0, p_stage_offset = 0;
+    int p_stage_floats = 0, p_stage_offset = 0, p_sp = 0;
     int n_tasks = 0;
     unsigned char *d_sched = nullptr;
     int4 *d_cta_sched = nullptr;
@@ -363,6 +363,8 @@ smre_status plan_persistent(smre_dykstra *h, int flags)
     // per-CTA schedule segments: TaskS[] | pass q offsets | dependency ids
     std::vector<unsigned char> sched;
     std::vector<int4> cta_sched(G);
+    const int sp = persist_smem_pitch(pitch);
+    if (sp == 0) return SMRE_OK;
     int maxL = 0, max_items = 1;
     double items_ratio = 0.0;   // max over tasks of items / items allowed per warp
     long long stage_floats = 0;
@@ -399,7 +401,7 @@ smre_status plan_persistent(smre_dykstra *h, int flags)
                 max_items = std::max(max_items, items);
                 items_ratio = std::max(items_ratio, (double)items / max_items_for_side(t.L));
             }
-            stage_floats = std::max(stage_floats, (long long)t.U * t.L * pitch);
+            stage_floats = std::max(stage_floats, (long long)t.U * t.L * sp);
             if (t.U * t.L > 64) return SMRE_OK;   // row mask would not fit
             ts.push_back(t);
         }
@@ -428,12 +430,10 @@ smre_status plan_persistent(smre_dykstra *h, int flags)
     if (budget < stage_offset + xs_bytes) return SMRE_OK;
     const long long fit = (long long)((budget - stage_offset - xs_bytes) / (stage_floats * 4));
     const int S = (int)std::min<long long>(kMaxStages, fit);
-    // warps without windows may run up to L passes ahead within a task, so
-    // the ring must hold more passes than the longest task
-    if (S < 3 || S <= maxL) return SMRE_OK;
+    if (S < 3) return SMRE_OK;
     const size_t smem = stage_offset + (size_t)S * stage_floats * 4 + xs_bytes;
     int occ = 0;
-    cudaError_t oe = persist_occupancy(maxL, threads, smem, &occ);
+    cudaError_t oe = persist_occupancy(sp, threads, smem, &occ);
     if (oe != cudaSuccess || occ < 1) {
         cudaGetLastError();
         return SMRE_OK;
@@ -455,9 +455,12 @@ smre_status plan_persistent(smre_dykstra *h, int flags)
     CK(h, cudaMemset(h->d_selftest, 0, 64));
     CK(h, cudaMalloc(&h->d_abort, 64));
     CK(h, cudaMalloc(&h->d_ppartials, sizeof(double) * 4 * G));
-    CK(h, cudaMalloc(&h->d_zeros, sizeof(float) * stage_floats));
-    CK(h, cudaMemset(h->d_zeros, 0, sizeof(float) * stage_floats));
-    h->dev_bytes += sizeof(float) * stage_floats;
+    // zero source of the first cycle's copies (at most one unit-pass of rows)
+    const size_t zero_floats = (size_t)stage_floats / sp * pitch;
+    CK(h, cudaMalloc(&h->d_zeros, sizeof(float) * zero_floats));
+    CK(h, cudaMemset(h->d_zeros, 0, sizeof(float) * zero_floats));
+    h->dev_bytes += sizeof(float) * zero_floats;
+    h->p_sp = sp;
     h->dev_bytes += sizeof(unsigned) * tasks.size() + 192 + sizeof(double) * 4 * G;
     h->n_tasks = (int)tasks.size();
     h->p_grid = G;
@@ -510,7 +513,7 @@ smre_status run_persistent(smre_dykstra *h)
     A.abort_word = h->d_abort;
     A.selftest_timeout = (h->flags & SMRE_F_SELFTEST_TIMEOUT) ? 1 : 0;
     A.selftest_flag = h->d_selftest;
-    CK(h, launch_persist(A, h->p_maxL, h->p_grid, h->p_threads, h->p_smem, h->stream));
+    CK(h, launch_persist(A, h->p_sp, h->p_grid, h->p_threads, h->p_smem, h->stream));
     h->launches += 1;
     return SMRE_OK;
 }

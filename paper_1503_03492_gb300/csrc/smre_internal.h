@@ -58,7 +58,7 @@ struct GroupArgs {
 // ---- persistent standard path (smre_persist.cu)
 
 constexpr int kMaxStages = 16;    // ring stages of the increment stream
-constexpr int kPersistThreads = 576;   // most threads per CTA of the persistent kernel
+constexpr int kPersistThreads = 640;   // most threads per CTA of the persistent kernel
 constexpr int kMaxItems = 4;          // (unit, window chunk) items per consumer warp and task
 // items a consumer warp may hold in one task of side L (register budget)
 __host__ __device__ constexpr int max_items_for_side(int L) { return L <= 4 ? 4 : (L <= 8 ? 2 : 1); }
@@ -109,7 +109,7 @@ struct PersistArgs {
     double tol;
     int tol_relative;
     int stages;
-    int stage_floats;            // floats per stage
+    int stage_floats;            // floats per stage (rows of the shared-memory stride)
     int stage_offset;            // bytes from the start of dynamic shared memory
     unsigned long long timeout_ns;
     int *abort_word;
@@ -118,8 +118,10 @@ struct PersistArgs {
 };
 
 bool persist_supported(int max_side);
-cudaError_t persist_occupancy(int max_side, int threads, size_t smem, int *blocks_per_sm);
-cudaError_t launch_persist(const PersistArgs &A, int max_side, int grid, int threads, size_t smem,
+// shared-memory row stride (power of two >= pitch, 128..1024) or 0 if too wide
+int persist_smem_pitch(int pitch);
+cudaError_t persist_occupancy(int sp, int threads, size_t smem, int *blocks_per_sm);
+cudaError_t launch_persist(const PersistArgs &A, int sp, int grid, int threads, size_t smem,
                            cudaStream_t s);
 
 // Launchers (defined next to their kernels).

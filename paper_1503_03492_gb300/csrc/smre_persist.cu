@@ -11,11 +11,11 @@
 // per cycle gathers the FP64 norms of the stopping test.
 //
 // Data movement:
-//  - increments q_s (the HBM stream, sum_L L^2 H W floats) move between HBM
-//    and a ring of shared-memory stages with bulk async copies (TMA engine):
-//    one elected thread keeps S-2 passes of loads in flight ahead of the
-//    consumers and writes each pass's updated increments back with a bulk
-//    store, so the copy engine streams while the CTA waits or computes;
+//  - increments q_s (the HBM stream, sum_L L^2 H W floats) come in through a
+//    ring of shared-memory stages filled by bulk async copies (TMA engine)
+//    that a producer warp keeps S passes ahead of the consumers; the
+//    consumers write the updated increments straight back to HBM with
+//    coalesced streaming stores;
 //  - x of the CTA's rows sits in registers for the L passes of a task; it goes
 //    through L2 only at task boundaries;
 //  - the cycle norm |x - x_prev|^2, |x_prev|^2 (FP64) is fused into the task
@@ -115,6 +115,11 @@ __device__ __forceinline__ void bulk_wait_read1()
 }
 
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+__device__ __forceinline__ void fence_proxy_async_global()
+{
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
 
 __device__ __forceinline__ void fence_proxy_async_smem()
 {
@@ -229,15 +234,18 @@ struct PassCtx {
     uint64_t *full, *written;
     float *stage0, *xs;
     volatile int *pass_abort;   // shared: set by a worker whose copy did not arrive
+    const long long *pass_qoff; // q offset of each pass of this CTA's cycle
     int S, NCW, NC, warp, lane, pitch;
 };
 
 // The L passes b = 0..L-1 of one task, side L known at compile time.  Returns
 // true when the launch must be abandoned (a copy did not arrive in time).
-template <int L>
+template <int L, int SP>
 __device__ __forceinline__ bool run_passes(const PassCtx &cx, const TaskS &ts, int &s_cur,
                                            unsigned &fph)
 {
+    // SP: row stride of x and of the stages in shared memory (compile time,
+    // so every shared-memory access of a pass uses an immediate offset)
     constexpr int wpw = 32 / L;                     // windows per warp
     constexpr int MI = max_items_for_side(L);       // items per warp and task
     const int lane = cx.lane, warp = cx.warp, pitch = cx.pitch;
@@ -248,31 +256,34 @@ __device__ __forceinline__ bool run_passes(const PassCtx &cx, const TaskS &ts, i
     const int nv0 = W / L, rem0 = W - nv0 * L;      // pass b has nv0 - (b > rem0) windows
     const int nwc = (nv0 + wpw - 1) / wpw;          // warp chunks per unit
     // this warp's (unit, chunk) items, fixed for the task's passes
-    int it_q[MI], it_v[MI];
+    int it_q[MI], it_g[MI], it_v[MI];
     int nit = 0;
 #pragma unroll
     for (int n = 0; n < MI; ++n) {
         const int item = warp + n * cx.NCW;
-        it_q[n] = 0;
+        it_q[n] = it_g[n] = 0;
         it_v[n] = 1 << 30;
         if (item < U * nwc) {
             const int j = item / nwc, k = item - j * nwc;
             it_v[n] = k * wpw + wl;
-            it_q[n] = j * L * pitch + it_v[n] * L + col;   // column offset (pass-relative)
+            it_q[n] = j * L * SP + it_v[n] * L + col;      // shared memory (pass-relative column)
+            it_g[n] = j * L * pitch + it_v[n] * L + col;   // the same column in HBM
             nit = n + 1;
         }
     }
     const int nwork = U * nwc < cx.NCW ? U * nwc : cx.NCW;   // warps holding items
     if (nit == 0) {
-        // no window of this task in this warp: release every pass's stage at
-        // once (the increments are untouched here) and wait at the task end
+        // no window of this task in this warp: follow the stages (the wait
+        // suspends the warp) and release each one untouched
+        bool bad = false;
         for (int b = 0; b < L; ++b) {
+            if (!bad) bad = !mbar_wait_timed(*cx.A, &cx.full[s_cur], (fph >> s_cur) & 1u);
             fph ^= 1u << s_cur;
             __syncwarp();
             if (lane == 0) mbar_arrive(&cx.written[s_cur]);
             s_cur = s_cur + 1 == cx.S ? 0 : s_cur + 1;
         }
-        return false;
+        return bad;
     }
     const float cS = ts.cS, sqrt_cS = ts.sqrt_cS;
     for (int b = 0; b < L; ++b) {
@@ -280,18 +291,20 @@ __device__ __forceinline__ bool run_passes(const PassCtx &cx, const TaskS &ts, i
         const bool bad = !mbar_wait_timed(*cx.A, &cx.full[s], (fph >> s) & 1u);
         fph ^= 1u << s;
         float *stg = cx.stage0 + (size_t)s * cx.A->stage_floats;
+        float *qg = cx.A->q + cx.pass_qoff[ts.pass0 + b];   // this pass's increments in HBM
         const int nv = b <= rem0 ? nv0 : nv0 - 1;
 #pragma unroll
         for (int n = 0; n < MI; ++n) {
             if (n >= nit) break;
             const bool on = lane_on && it_v[n] < nv;
             float *xr = cx.xs + it_q[n] + b;
-            float *qr = stg + it_q[n];
+            const float *qr = stg + it_q[n];
+            float *qw = qg + it_g[n];
             float y[L];
             float sq = 0.f;
             if (on) {
 #pragma unroll
-                for (int i = 0; i < L; ++i) y[i] = xr[i * pitch] + qr[i * pitch];
+                for (int i = 0; i < L; ++i) y[i] = xr[i * SP] + qr[i * SP];
 #pragma unroll
                 for (int i = 0; i < L; ++i) sq = fmaf(y[i], y[i], sq);
             }
@@ -318,14 +331,13 @@ __device__ __forceinline__ bool run_passes(const PassCtx &cx, const TaskS &ts, i
 #pragma unroll
                 for (int i = 0; i < L; ++i) {
                     const float xn = y[i] * scale;
-                    xr[i * pitch] = xn;
-                    qr[i * pitch] = y[i] - xn;
+                    xr[i * SP] = xn;
+                    __stcs(qw + i * pitch, y[i] - xn);   // streaming store: read again next cycle
                 }
             }
         }
-        fence_proxy_async_smem();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&cx.written[s]);
+        if (lane == 0) mbar_arrive(&cx.written[s]);   // this warp is done reading the stage
         s_cur = s + 1 == cx.S ? 0 : s + 1;
         if (bad) *cx.pass_abort = 1;
         workers_sync(nwork * 32);                         // orders xs between passes
@@ -334,11 +346,12 @@ __device__ __forceinline__ bool run_passes(const PassCtx &cx, const TaskS &ts, i
     return false;
 }
 
+template <int SP>
 __device__ __forceinline__ bool run_task_passes(const PassCtx &cx, const TaskS &ts, int &s_cur,
-                                             unsigned &fph)
+                                                unsigned &fph)
 {
     switch (ts.L) {
-#define RP(l) case l: return run_passes<l>(cx, ts, s_cur, fph);
+#define RP(l) case l: return run_passes<l, SP>(cx, ts, s_cur, fph);
         RP(1) RP(2) RP(3) RP(4) RP(5) RP(6) RP(7) RP(8)
         RP(9) RP(10) RP(11) RP(12) RP(13) RP(14) RP(15) RP(16)
 #undef RP
@@ -355,14 +368,15 @@ enum { kGo = 0, kStop = 1, kAbort = 2 };
 //   full[s]    completes when stage s holds the increments of its next pass
 //              (bulk load; in the first cycle q = 0 and a plain arrive only
 //              hands the empty stage over)
-//   written[s] completes when every consumer warp has written the pass's new
-//              increments into stage s, so the producer can store them and
-//              then refill the stage S passes ahead.
+//   written[s] completes when every consumer warp is done reading stage s
+//              (the new increments go straight to HBM with ordinary stores),
+//              so the producer can refill the stage S passes ahead.
 // In pass b of a task the consumer lanes map onto windows: with
 // wpw = floor(32 / L) windows per warp, lane l takes column l % L of window
 // k * wpw + l / L of its warp's chunk k; a window's column sums meet by
 // shuffles in a fixed order, so every lane of a window sees the same sum.
 // x of the task's rows lives in shared memory for the task's L passes.
+template <int SP>
 __global__ void __launch_bounds__(kPersistThreads, 1) persist_kernel(const PersistArgs A)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -372,7 +386,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1) persist_kernel(const Persi
     int *s_prov = reinterpret_cast<int *>(written + kMaxStages);      // [S] provides per stage
     unsigned char *tbl = smem + 512;                                  // schedule
     float *stage0 = reinterpret_cast<float *>(smem + A.stage_offset); // [S][stage_floats]
-    float *xs = stage0 + (size_t)S * A.stage_floats;                  // [rows][pitch]
+    float *xs = stage0 + (size_t)S * A.stage_floats;                  // [rows][SP]
     __shared__ int s_dec, s_abort;
     __shared__ volatile int s_pass_abort;
     __shared__ double s_red[2][32];
@@ -420,14 +434,21 @@ __global__ void __launch_bounds__(kPersistThreads, 1) persist_kernel(const Persi
                 auto provide = [&](int task, int b, int stg) {
                     s_prov[stg] += 1;
                     const TaskS &ts = tasks_s[task];
-                    const unsigned unit_bytes = (unsigned)(ts.L * pitch * sizeof(float));
-                    mbar_arrive_expect_tx(&full[stg], unit_bytes * ts.U);
+                    const unsigned row_bytes = (unsigned)(pitch * sizeof(float));
+                    mbar_arrive_expect_tx(&full[stg], row_bytes * ts.L * ts.U);
                     // the first cycle starts from q = 0: copy from a zeroed block
                     const float *src = first ? A.zeros : A.q + pass_qoff[ts.pass0 + b];
                     float *dst = stage0 + (size_t)stg * A.stage_floats;
-                    for (int j = 0; j < ts.U; ++j)
-                        bulk_load(dst + (size_t)j * ts.L * pitch,
-                                  first ? src : src + (size_t)j * ts.L * pitch, unit_bytes, &full[stg]);
+                    if (pitch == SP) {         // one contiguous block per unit
+                        for (int j = 0; j < ts.U; ++j)
+                            bulk_load(dst + (size_t)j * ts.L * SP,
+                                      first ? src : src + (size_t)j * ts.L * pitch,
+                                      row_bytes * ts.L, &full[stg]);
+                    } else {                   // row by row into SP-strided rows
+                        for (int r = 0; r < ts.L * ts.U; ++r)
+                            bulk_load(dst + (size_t)r * SP, first ? src : src + (size_t)r * pitch,
+                                      row_bytes, &full[stg]);
+                    }
                 };
                 int rt = 0, rb = 0, rs = s_head;       // refill cursor
                 const int pre = npass < S ? npass : S;
@@ -436,36 +457,28 @@ __global__ void __launch_bounds__(kPersistThreads, 1) persist_kernel(const Persi
                     if (++rb == tasks_s[rt].L) { rb = 0; ++rt; }
                     rs = rs + 1 == S ? 0 : rs + 1;
                 }
-                int t = 0, bb = 0;                     // store cursor
                 for (int p = 0; p < npass; ++p) {
+                    // consumers have read the stage of pass p: refill it S passes ahead
                     if (!mbar_wait_timed(A, &written[s_head], (wph >> s_head) & 1u)) {
                         dead = true;
                         break;
                     }
                     wph ^= 1u << s_head;
-                    const TaskS &ts = tasks_s[t];
-                    const unsigned unit_bytes = (unsigned)(ts.L * pitch * sizeof(float));
-                    float *dq = A.q + pass_qoff[ts.pass0 + bb];
-                    const float *sq = stage0 + (size_t)s_head * A.stage_floats;
-                    for (int j = 0; j < ts.U; ++j)
-                        bulk_store(dq + (size_t)j * ts.L * pitch, sq + (size_t)j * ts.L * pitch,
-                                   unit_bytes);
-                    bulk_commit();
                     if (p + S < npass) {
-                        bulk_wait_read0();     // the store has read the stage out
                         provide(rt, rb, s_head);
                         if (++rb == tasks_s[rt].L) { rb = 0; ++rt; }
                     }
-                    if (++bb == ts.L) { bb = 0; ++t; }
                     s_head = s_head + 1 == S ? 0 : s_head + 1;
                 }
-                bulk_wait_all();               // this cycle's stores have landed
             }
             __syncwarp();
             cta_sync_all();                    // consumers publish the decision
             const int dec = s_dec;
             cta_sync_all();
             if (dec != kGo || dead) break;
+            // the consumers stored this cycle's increments with ordinary stores;
+            // order them before the bulk (async-proxy) loads of the next cycle
+            fence_proxy_async_global();
         }
         if (lane == 0) {
             // let every load in flight land before the shared memory is released
@@ -481,7 +494,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1) persist_kernel(const Persi
     }
 
     // ======================================================== consumer warps
-    const PassCtx cx{&A, full, written, stage0, xs, &s_pass_abort, S, NCW, NC, warp, lane, pitch};
+    const PassCtx cx{&A, full, written, stage0, xs, &s_pass_abort, pass_qoff, S, NCW, NC, warp, lane, pitch};
     int s_cur = 0;
     unsigned fph = 0;            // parity of the next `full` wait, per stage
     double d2 = 0.0, n2 = 0.0;   // this thread's share of the cycle norm
@@ -508,27 +521,32 @@ __global__ void __launch_bounds__(kPersistThreads, 1) persist_kernel(const Persi
 
             // x rows of the task into shared memory (from L2)
             {
+                const int q4 = pitch / 4;
                 const float4 *src = reinterpret_cast<const float4 *>(A.x + (size_t)ts.r_first * pitch);
                 float4 *dst = reinterpret_cast<float4 *>(xs);
-                const int n4 = rows * pitch / 4;
-                for (int i = tid; i < n4; i += NC) dst[i] = __ldcg(src + i);
+                const int n4 = rows * q4;
+                for (int i = tid; i < n4; i += NC) {
+                    const int rr = i / q4, c4 = i - rr * q4;
+                    dst[rr * (SP / 4) + c4] = __ldcg(src + i);
+                }
             }
             consumers_sync(NC);
 
             {
-                const bool ab = run_task_passes(cx, ts, s_cur, fph);
+                const bool ab = run_task_passes<SP>(cx, ts, s_cur, fph);
                 if (consumers_sync_or(ab, NC)) aborted = true;   // xs complete for the store
             }
             if (aborted) break;
 
             // x back to L2; fused cycle norm on the rows this task touches last
             {
-                const int n4 = rows * pitch / 4;
                 const int q4 = pitch / 4;
+                const int n4 = rows * q4;
                 float4 *dst = reinterpret_cast<float4 *>(A.x + (size_t)ts.r_first * pitch);
                 const float4 *src = reinterpret_cast<const float4 *>(xs);
                 for (int i = tid; i < n4; i += NC) {
-                    const float4 v = src[i];
+                    const int rs = i / q4;
+                    const float4 v = src[rs * (SP / 4) + (i - rs * q4)];
                     dst[i] = v;
                     const int rr = i / q4;
                     const int c4 = (i - rr * q4) * 4;
@@ -549,10 +567,8 @@ __global__ void __launch_bounds__(kPersistThreads, 1) persist_kernel(const Persi
                 }
             }
             consumers_sync(NC);
-            if (tid == 0) {
-                __threadfence();
+            if (tid == 0)   // release: the CTA's x stores (ordered by the barrier) before the flag
                 st_release(A.flags + ts.gid, (unsigned)(cyc + 1));
-            }
         }
 
         // ---- end of cycle: publish norms, grid barrier, same decision everywhere
@@ -635,6 +651,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1) persist_kernel(const Persi
                 }
             }
         }
+        fence_proxy_async_global();   // this cycle's increment stores before next cycle's bulk loads
         if (tid == 0) s_dec = dec;
         cta_sync_all();
         cta_sync_all();
@@ -642,34 +659,58 @@ __global__ void __launch_bounds__(kPersistThreads, 1) persist_kernel(const Persi
     }
 }
 
+template <int SP>
 cudaError_t launch_persist_t(const PersistArgs &A, int grid, int threads, size_t smem,
                              cudaStream_t s)
 {
-    auto k = persist_kernel;
+    auto k = persist_kernel<SP>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     void *args[] = {const_cast<PersistArgs *>(&A)};
     return cudaLaunchCooperativeKernel((const void *)k, dim3(grid), dim3(threads), args, smem, s);
 }
 
+const void *kernel_for(int sp)
+{
+    switch (sp) {
+        case 128: return (const void *)persist_kernel<128>;
+        case 256: return (const void *)persist_kernel<256>;
+        case 512: return (const void *)persist_kernel<512>;
+        case 1024: return (const void *)persist_kernel<1024>;
+        default: return nullptr;
+    }
+}
+
 }  // namespace
+
+int persist_smem_pitch(int pitch)
+{
+    int sp = 128;
+    while (sp < pitch) sp *= 2;
+    return sp <= 1024 ? sp : 0;
+}
 
 bool persist_supported(int max_side) { return max_side >= 1 && max_side <= 16; }
 
-cudaError_t persist_occupancy(int max_side, int threads, size_t smem, int *blocks_per_sm)
+cudaError_t persist_occupancy(int sp, int threads, size_t smem, int *blocks_per_sm)
 {
-    (void)max_side;
-    const void *k = (const void *)persist_kernel;
+    const void *k = kernel_for(sp);
+    if (!k) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, threads, smem);
 }
 
-cudaError_t launch_persist(const PersistArgs &A, int max_side, int grid, int threads, size_t smem,
+cudaError_t launch_persist(const PersistArgs &A, int sp, int grid, int threads, size_t smem,
                            cudaStream_t s)
 {
-    (void)max_side;
-    return launch_persist_t(A, grid, threads, smem, s);
+    switch (sp) {
+        case 128: return launch_persist_t<128>(A, grid, threads, smem, s);
+        case 256: return launch_persist_t<256>(A, grid, threads, smem, s);
+        case 512: return launch_persist_t<512>(A, grid, threads, smem, s);
+        case 1024: return launch_persist_t<1024>(A, grid, threads, smem, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace smre
