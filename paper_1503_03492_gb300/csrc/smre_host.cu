@@ -64,7 +64,7 @@ struct smre_dykstra {
     int p_stage_floats = 0, p_stage_offset = 0, p_sp = 0;
     int n_tasks = 0;
     unsigned char *d_sched = nullptr;
-    int4 *d_cta_sched = nullptr;
+    int *d_cta_off = nullptr;
     int p_sched_bytes = 0;
     unsigned *d_flags = nullptr, *d_barrier = nullptr, *d_selftest = nullptr;
     double *d_ppartials = nullptr;
@@ -297,10 +297,16 @@ smre_status violation(smre_dykstra *h, double &out)
     return SMRE_OK;
 }
 
-// Plan of the persistent kernel: home bands of rows per CTA, tasks, the flags
-// each task waits for, the last toucher of every row, and the stage ring.
-// Leaves h->persist false when the shape does not fit it (the group-launch
-// path then runs instead).
+// Plan of the persistent kernel.  For every side L the window-rows ("units")
+// u = 0..n_u(0)-1 of the side are split into contiguous ranges, one per CTA,
+// spread over the CTAs; a CTA keeps its range for all offsets a = 0..L-1 of
+// the side (the band of U*L rows slides down one row per offset).  Events
+// (side L, CTA c, offset a) publish rows: the band's top row after offsets
+// a < L-1, the whole band after a = L-1; each event has a flag.  The plan
+// gives every side task the flags of the previous sides' last publishers of
+// the rows it may read, every offset the flag of the neighbour whose top row
+// it takes over, and the rows each event publishes for the last time in a
+// cycle (fused norm).  Leaves h->persist false when the shape does not fit.
 smre_status plan_persistent(smre_dykstra *h, int flags)
 {
     h->persist = false;
@@ -310,110 +316,167 @@ smre_status plan_persistent(smre_dykstra *h, int flags)
     CK(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     CK(h, cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     const int H = h->H, W = h->W, pitch = h->pitch;
-    const int G = std::max(1, std::min(sms, H));
-    auto owner = [&](int r) { return (int)(((long long)r * G) / H); };
-
-    // tasks per (group, CTA), in cycle order
-    struct T0 { int g, c, ub, ue; };
-    std::vector<T0> tasks;
-    for (int g = 0; g < (int)h->groups.size(); ++g) {
-        const Group &gr = h->groups[g];
-        int u = 0;
-        while (u < gr.n_units) {
-            const int c = owner(gr.a + gr.L * u);
-            int v = u + 1;
-            while (v < gr.n_units && owner(gr.a + gr.L * v) == c) ++v;
-            tasks.push_back({g, c, u, v});
-            u = v;
-        }
-    }
-    // dependencies on the last toucher of each row (other CTAs only)
-    std::vector<int> last(H, -1);
-    std::vector<std::vector<int>> deps(tasks.size());
-    size_t t = 0;
-    while (t < tasks.size()) {
-        size_t e = t;
-        while (e < tasks.size() && tasks[e].g == tasks[t].g) ++e;
-        for (size_t k = t; k < e; ++k) {
-            const Group &gr = h->groups[tasks[k].g];
-            const int r0 = gr.a + gr.L * tasks[k].ub, r1 = gr.a + gr.L * tasks[k].ue;
-            for (int r = r0; r < r1; ++r) {
-                const int d = last[r];
-                if (d >= 0 && tasks[d].c != tasks[k].c &&
-                    std::find(deps[k].begin(), deps[k].end(), d) == deps[k].end())
-                    deps[k].push_back(d);
-            }
-        }
-        for (size_t k = t; k < e; ++k) {
-            const Group &gr = h->groups[tasks[k].g];
-            for (int r = gr.a + gr.L * tasks[k].ub; r < gr.a + gr.L * tasks[k].ue; ++r) last[r] = (int)k;
-        }
-        t = e;
-    }
-    // order tasks by (CTA, cycle order) and renumber
-    std::vector<int> order(tasks.size());
-    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return tasks[a].c < tasks[b].c; });
-    std::vector<int> newid(tasks.size());
-    for (size_t i = 0; i < order.size(); ++i) newid[order[i]] = (int)i;
-    std::vector<int> final_task(H, -1);
-    for (int r = 0; r < H; ++r)
-        if (last[r] >= 0) final_task[r] = newid[last[r]];
-
-    // per-CTA schedule segments: TaskS[] | pass q offsets | dependency ids
-    std::vector<unsigned char> sched;
-    std::vector<int4> cta_sched(G);
     const int sp = persist_smem_pitch(pitch);
     if (sp == 0) return SMRE_OK;
-    int maxL = 0, max_items = 1;
-    double items_ratio = 0.0;   // max over tasks of items / items allowed per warp
+    const int G = std::max(1, std::min(sms, H));
+
+    std::vector<int> sides_desc(h->sides.rbegin(), h->sides.rend());
+    struct Side0 {
+        int L, c, u0, u1;
+        std::vector<int> deps;        // flag ids
+        std::vector<int> nb;          // per offset: neighbour flag or -1
+        std::vector<int> Ua;          // per offset: units present
+        unsigned top_final = 0;
+        unsigned long long end_final = 0;
+        int flag0 = 0;
+    };
+    std::vector<Side0> st;            // in cycle order (sides descending), CTA ascending
+    std::vector<int> last_pub(H, -1), last_pub_cta(H, -1);
+    std::vector<int> ev_of_row(H, -1);   // for the final masks: (side task index, kind)
+    struct Pub { int task, a; };          // a = -1: side end
+    std::vector<Pub> last_event(H, {-1, 0});
+    int nflags = 0;
+    int maxL = 0;
+    for (int L : sides_desc) {
+        maxL = std::max(maxL, L);
+        std::vector<int> nu(L);
+        for (int a = 0; a < L; ++a) nu[a] = (H - a) / L;
+        const int n0 = nu[0];
+        if (n0 <= 0) continue;
+        // unit ranges: unit u belongs to CTA floor(u G / n0) (spread over all CTAs)
+        std::vector<int> owner(n0);
+        for (int u = 0; u < n0; ++u) owner[u] = (int)(((long long)u * G) / n0);
+        const size_t first_task = st.size();
+        for (int u = 0; u < n0;) {
+            int v = u + 1;
+            while (v < n0 && owner[v] == owner[u]) ++v;
+            Side0 t;
+            t.L = L;
+            t.c = owner[u];
+            t.u0 = u;
+            t.u1 = v;
+            t.flag0 = nflags;
+            nflags += L;
+            t.Ua.resize(L);
+            t.nb.assign(L, -1);
+            for (int a = 0; a < L; ++a) t.Ua[a] = std::max(0, std::min(v, nu[a]) - u);
+            st.push_back(t);
+            u = v;
+        }
+        // side-start dependencies: last publishers (other CTAs) of every row a
+        // task may read during the side: [L u0, L u0 + U L + L - 1)
+        for (size_t k = first_task; k < st.size(); ++k) {
+            Side0 &t = st[k];
+            const int r0 = t.L * t.u0, r1 = std::min(H, r0 + (t.u1 - t.u0) * t.L + t.L - 1);
+            for (int r = r0; r < r1; ++r) {
+                const int f = last_pub[r];
+                if (f >= 0 && last_pub_cta[r] != t.c &&
+                    std::find(t.deps.begin(), t.deps.end(), f) == t.deps.end())
+                    t.deps.push_back(f);
+            }
+        }
+        // neighbour flags: at offset a >= 1 the task takes row (a-1) + L u1, the top
+        // row its lower neighbour (the task owning unit u1) published after offset
+        // a-1 -- the neighbour slides and publishes at every offset, with or without
+        // units, so it holds that row's latest value; the last task reads it from
+        // the image (no task of this side touched it; the side-start flags cover it)
+        for (size_t k = first_task; k < st.size(); ++k) {
+            Side0 &t = st[k];
+            const bool has_nb = k + 1 < st.size() && st[k + 1].L == L;
+            for (int a = 1; a < L; ++a)
+                if (has_nb) t.nb[a] = st[k + 1].flag0 + (a - 1);
+        }
+        // events of the side, in order: top rows after a < L-1, bands at a = L-1
+        for (int a = 0; a < L; ++a)
+            for (size_t k = first_task; k < st.size(); ++k) {
+                Side0 &t = st[k];
+                const int band = (t.u1 - t.u0) * L;
+                const int top = a + L * t.u0;
+                const int f = t.flag0 + a;
+                if (a < L - 1) {
+                    last_pub[top] = f;
+                    last_pub_cta[top] = t.c;
+                    last_event[top] = {(int)k, a};
+                } else {
+                    for (int i = 0; i < band && top + i < H; ++i) {
+                        last_pub[top + i] = f;
+                        last_pub_cta[top + i] = t.c;
+                        last_event[top + i] = {(int)k, -1 - i};
+                    }
+                }
+            }
+    }
+    // rows published for the last time in the cycle: norm there
+    for (int r = 0; r < H; ++r) {
+        const Pub e = last_event[r];
+        if (e.task < 0) return SMRE_OK;   // a row no side touches: keep the group path
+        if (e.a >= 0) st[e.task].top_final |= 1u << e.a;
+        else st[e.task].end_final |= 1ull << (-1 - e.a);
+    }
+
+    // per-CTA schedule segments: header | SideS[] | GrpS[] | pass q offsets | deps
+    std::vector<unsigned char> sched;
+    std::vector<int> cta_off(G, 0);
+    int max_items = 1;
+    double items_ratio = 0.0;
     long long stage_floats = 0;
     size_t seg_max = 16;
-    size_t i = 0;
     for (int c = 0; c < G; ++c) {
-        std::vector<TaskS> ts;
+        std::vector<SideS> ss;
+        std::vector<GrpS> gs;
         std::vector<long long> qo;
         std::vector<int> dl;
-        for (; i < order.size() && tasks[order[i]].c == c; ++i) {
-            const T0 &o = tasks[order[i]];
-            const Group &gr = h->groups[o.g];
-            TaskS t{};
-            t.L = gr.L;
-            t.U = o.ue - o.ub;
-            t.r_first = gr.a + gr.L * o.ub;
-            t.gid = (int)i;
-            t.dep_begin = (int)dl.size();
-            for (int d : deps[order[i]]) dl.push_back(newid[d]);
-            t.dep_count = (int)dl.size() - t.dep_begin;
-            t.pass0 = (int)qo.size();
-            t.cS = (float)h->cS_of[gr.L];
-            t.sqrt_cS = (float)std::sqrt(h->cS_of[gr.L]);
-            t.cS64 = h->cS_of[gr.L];
-            t.final_mask = 0;
-            for (int r = t.r_first; r < t.r_first + t.U * t.L; ++r)
-                if (final_task[r] == (int)i) t.final_mask |= 1ull << (r - t.r_first);
-            for (int bb = 0; bb < gr.L; ++bb)
-                qo.push_back(h->tilings[gr.tiling0 + bb].q_off + (long long)o.ub * gr.L * pitch);
-            maxL = std::max(maxL, t.L);
-            {
-                const int wpw = 32 / t.L, nv = W / t.L;
-                const int items = t.U * ((nv + wpw - 1) / wpw);
-                max_items = std::max(max_items, items);
-                items_ratio = std::max(items_ratio, (double)items / max_items_for_side(t.L));
+        // tiling index of (L, a, 0): offset in the cycle order
+        for (size_t k = 0; k < st.size(); ++k) {
+            const Side0 &t = st[k];
+            if (t.c != c) continue;
+            const int L = t.L, U = t.u1 - t.u0;
+            if (U * L > 64) return SMRE_OK;      // final masks are 64-bit
+            SideS x{};
+            x.L = L;
+            x.U = U;
+            x.r0 = L * t.u0;
+            x.dep_begin = (int)dl.size();
+            for (int f : t.deps) dl.push_back(f);
+            x.dep_count = (int)dl.size() - x.dep_begin;
+            x.grp0 = (int)gs.size();
+            x.pass0 = (int)qo.size();
+            x.flag0 = t.flag0;
+            x.top_final = t.top_final;
+            x.end_final = t.end_final;
+            x.cS = (float)h->cS_of[L];
+            x.sqrt_cS = (float)std::sqrt(h->cS_of[L]);
+            x.cS64 = h->cS_of[L];
+            int g_index = -1;
+            for (size_t g = 0; g < h->groups.size(); ++g)
+                if (h->groups[g].L == L && h->groups[g].a == 0) g_index = (int)g;
+            for (int a = 0; a < L; ++a) {
+                gs.push_back({t.Ua[a], t.nb[a]});
+                const Group &gr = h->groups[g_index + a];
+                for (int b = 0; b < L; ++b)
+                    qo.push_back(h->tilings[gr.tiling0 + b].q_off + (long long)t.u0 * L * pitch);
             }
-            stage_floats = std::max(stage_floats, (long long)t.U * t.L * sp);
-            if (t.U * t.L > 64) return SMRE_OK;   // row mask would not fit
-            ts.push_back(t);
+            ss.push_back(x);
+            const int wpw = 32 / L, nv = W / L;
+            const int items = U * ((nv + wpw - 1) / wpw);
+            max_items = std::max(max_items, items);
+            items_ratio = std::max(items_ratio, (double)items / max_items_for_side(L));
+            stage_floats = std::max(stage_floats, (long long)U * L * sp);
         }
-        const size_t bytes = sizeof(TaskS) * ts.size() + sizeof(long long) * qo.size() +
-                             sizeof(int) * dl.size();
+        const int hdr[4] = {(int)ss.size(), (int)gs.size(), (int)qo.size(), (int)dl.size()};
+        const size_t bytes = sizeof(hdr) + sizeof(SideS) * ss.size() + sizeof(GrpS) * gs.size() +
+                             sizeof(long long) * qo.size() + sizeof(int) * dl.size();
         const size_t padded = (bytes + 15) / 16 * 16;
-        cta_sched[c] = make_int4((int)sched.size(), (int)ts.size(), (int)qo.size(), (int)dl.size());
+        cta_off[c] = (int)sched.size();
         const size_t at = sched.size();
-        sched.resize(at + std::max<size_t>(padded, 16), 0);
+        sched.resize(at + padded, 0);
         unsigned char *w = sched.data() + at;
-        memcpy(w, ts.data(), sizeof(TaskS) * ts.size());
-        w += sizeof(TaskS) * ts.size();
+        memcpy(w, hdr, sizeof(hdr));
+        w += sizeof(hdr);
+        memcpy(w, ss.data(), sizeof(SideS) * ss.size());
+        w += sizeof(SideS) * ss.size();
+        memcpy(w, gs.data(), sizeof(GrpS) * gs.size());
+        w += sizeof(GrpS) * gs.size();
         memcpy(w, qo.data(), sizeof(long long) * qo.size());
         w += sizeof(long long) * qo.size();
         memcpy(w, dl.data(), sizeof(int) * dl.size());
@@ -424,7 +487,7 @@ smre_status plan_persistent(smre_dykstra *h, int flags)
     const int ncw = std::max(4, std::min(kPersistThreads / 32 - 1, max_items));
     if (items_ratio > ncw) return SMRE_OK;   // too many items per warp
     const int threads = (ncw + 1) * 32;
-    const size_t xs_bytes = (size_t)stage_floats * 4;   // the largest task's rows
+    const size_t xs_bytes = (size_t)stage_floats * 4;   // the largest band
     const size_t stage_offset = 512 + (seg_max + 127) / 128 * 128;
     const size_t budget = (size_t)smem_optin - 1024;   // static shared memory and slack
     if (budget < stage_offset + xs_bytes) return SMRE_OK;
@@ -448,21 +511,21 @@ smre_status plan_persistent(smre_dykstra *h, int flags)
         return cudaMemcpy(*dptr, vec.data(), sizeof(E) * vec.size(), cudaMemcpyHostToDevice);
     };
     CK(h, up(&h->d_sched, sched));
-    CK(h, up(&h->d_cta_sched, cta_sched));
-    CK(h, cudaMalloc(&h->d_flags, sizeof(unsigned) * std::max<size_t>(tasks.size(), 1)));
+    CK(h, up(&h->d_cta_off, cta_off));
+    CK(h, cudaMalloc(&h->d_flags, sizeof(unsigned) * std::max(nflags, 1)));
     CK(h, cudaMalloc(&h->d_barrier, 64));
     CK(h, cudaMalloc(&h->d_selftest, 64));
     CK(h, cudaMemset(h->d_selftest, 0, 64));
     CK(h, cudaMalloc(&h->d_abort, 64));
     CK(h, cudaMalloc(&h->d_ppartials, sizeof(double) * 4 * G));
-    // zero source of the first cycle's copies (at most one unit-pass of rows)
+    // zero source of the first cycle's copies (one unit-pass of rows at most)
     const size_t zero_floats = (size_t)stage_floats / sp * pitch;
     CK(h, cudaMalloc(&h->d_zeros, sizeof(float) * zero_floats));
     CK(h, cudaMemset(h->d_zeros, 0, sizeof(float) * zero_floats));
-    h->dev_bytes += sizeof(float) * zero_floats;
+    h->dev_bytes += sizeof(unsigned) * nflags + 192 + sizeof(double) * 4 * G +
+                    sizeof(float) * zero_floats;
+    h->n_tasks = nflags;
     h->p_sp = sp;
-    h->dev_bytes += sizeof(unsigned) * tasks.size() + 192 + sizeof(double) * 4 * G;
-    h->n_tasks = (int)tasks.size();
     h->p_grid = G;
     h->p_threads = threads;
     h->p_stages = S;
@@ -495,7 +558,7 @@ smre_status run_persistent(smre_dykstra *h)
     A.W = h->W;
     A.consumer_warps = h->p_ncw;
     A.sched = h->d_sched;
-    A.cta_sched = h->d_cta_sched;
+    A.cta_off = h->d_cta_off;
     A.sched_bytes = h->p_sched_bytes;
     A.flags = h->d_flags;
     A.barrier = h->d_barrier;
@@ -874,7 +937,7 @@ void smre_dykstra_destroy(smre_dykstra *h)
     cudaFree(h->icd_sweeps);
     cudaFree(h->viol);
     cudaFree(h->d_sched);
-    cudaFree(h->d_cta_sched);
+    cudaFree(h->d_cta_off);
     cudaFree(h->d_flags);
     cudaFree(h->d_barrier);
     cudaFree(h->d_selftest);

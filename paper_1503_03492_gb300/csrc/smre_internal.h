@@ -76,18 +76,27 @@ struct GroupDesc {
     double cS64;
 };
 
-// Per-CTA schedule entry kept in shared memory for the whole launch.
-struct TaskS {
-    int r_first;                  // first image row of the task's units
-    int L, U;                     // side and number of units
-    int gid;                      // global task id (index of its flag)
-    int dep_begin, dep_count;     // range in the CTA's dependency list
-    int pass0;                    // first entry in the CTA's pass table
-    float cS;
-    float sqrt_cS;                // sqrt(cS) in FP32: scale = sqrt(cS) * rsqrt(t)
+// Per-CTA schedule, kept in shared memory for the whole launch: one entry per
+// side the CTA takes part in (cycle order), then per offset a of that side a
+// GrpS, then the q offsets of every pass (a-major, b minor), then flag ids.
+struct SideS {
+    int L, U;                     // side; units held (the band has U*L rows)
+    int r0;                       // first band row at offset a = 0 (L * u0)
+    int dep_begin, dep_count;     // side-start flags in the CTA's dependency list
+    int grp0;                     // first GrpS entry of the side
+    int pass0;                    // first pass q offset of the side
+    int flag0;                    // flag of event (side, this CTA, a = 0); a adds a
+    unsigned top_final;           // bit a: the top row published after offset a is final
+    float cS, sqrt_cS;            // bound of side L (FP32) and its square root
     int pad_;
-    unsigned long long final_mask;  // bit j*L+i: row r_first+j*L+i is final in this task
+    unsigned long long end_final; // bit k: band row k published at the side end is final
     double cS64;
+};
+
+struct GrpS {
+    int U;                        // units present at this offset
+    int nb_flag;                  // flag to wait before taking the lower neighbour's
+                                  // top row at this offset (a >= 1), or -1
 };
 
 struct PersistArgs {
@@ -95,11 +104,12 @@ struct PersistArgs {
     const float *zeros;          // stage_floats zero floats (increments of the first cycle)
     int pitch, H, W;
     int consumer_warps;          // warps 0..consumer_warps-1 consume, the next one produces
-    // per-CTA schedule: TaskS[n_tasks] | long long pass_qoff[n_passes] | int deps[n_deps]
+    // per-CTA schedule: int hdr[4] = {n_sides, n_grp, n_pass, n_dep} | SideS[] | GrpS[] |
+    // long long pass_qoff[] | int deps[]
     const unsigned char *sched;
-    const int4 *cta_sched;       // [G]: byte offset, n_tasks, n_passes, n_deps
+    const int *cta_off;          // [G]: byte offset of each CTA's segment
     int sched_bytes;             // shared-memory bytes reserved for the largest segment
-    unsigned *flags;             // [n_tasks] cycle + 1 once the task is done
+    unsigned *flags;             // [n_events] cycle + 1 once the event's rows are published
     unsigned *barrier;           // grid barrier counter
     double *partials;            // [2][G][2] per-CTA norms, double-buffered by cycle
     Control *ctl;

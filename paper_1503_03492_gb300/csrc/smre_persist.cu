@@ -228,6 +228,14 @@ __device__ __forceinline__ void workers_sync(int nthreads)
     else asm volatile("barrier.sync 2, %0;" ::"r"(nthreads) : "memory");
 }
 
+// One offset a of a side task as the passes see it.
+struct PassTask {
+    int L, U;          // side, units present at this offset (band rows 0 .. U*L-1)
+    int pass0;         // q offset entry of pass b = 0
+    float cS, sqrt_cS;
+    double cS64;
+};
+
 // Everything a consumer warp needs to run the passes of one task.
 struct PassCtx {
     const PersistArgs *A;
@@ -241,7 +249,7 @@ struct PassCtx {
 // The L passes b = 0..L-1 of one task, side L known at compile time.  Returns
 // true when the launch must be abandoned (a copy did not arrive in time).
 template <int L, int SP>
-__device__ __forceinline__ bool run_passes(const PassCtx &cx, const TaskS &ts, int &s_cur,
+__device__ __forceinline__ bool run_passes(const PassCtx &cx, const PassTask &ts, int &s_cur,
                                            unsigned &fph)
 {
     // SP: row stride of x and of the stages in shared memory (compile time,
@@ -347,7 +355,7 @@ __device__ __forceinline__ bool run_passes(const PassCtx &cx, const TaskS &ts, i
 }
 
 template <int SP>
-__device__ __forceinline__ bool run_task_passes(const PassCtx &cx, const TaskS &ts, int &s_cur,
+__device__ __forceinline__ bool run_task_passes(const PassCtx &cx, const PassTask &ts, int &s_cur,
                                                 unsigned &fph)
 {
     switch (ts.L) {
@@ -357,6 +365,72 @@ __device__ __forceinline__ bool run_task_passes(const PassCtx &cx, const TaskS &
 #undef RP
         default: return true;
     }
+}
+
+// Rows r_first .. r_first + n - 1 of the image (those inside it) into shared
+// memory rows k0 .. k0 + n - 1 (row stride SP), by the consumer threads.
+template <int SP>
+__device__ __forceinline__ void load_rows(const PersistArgs &A, float *xs, int k0, int r_first,
+                                          int n, int tid, int NC)
+{
+    const int q4 = A.pitch / 4;
+    const int rows = min(n, A.H - r_first);
+    if (rows <= 0) return;
+    const float4 *src = reinterpret_cast<const float4 *>(A.x + (size_t)r_first * A.pitch);
+    float4 *dst = reinterpret_cast<float4 *>(xs + (size_t)k0 * SP);
+    const int n4 = rows * q4;
+    for (int i = tid; i < n4; i += NC) {
+        const int rr = i / q4, c4 = i - rr * q4;
+        dst[rr * (SP / 4) + c4] = __ldcg(src + i);
+    }
+}
+
+// Shared-memory rows 0 .. n-1 back to image rows r_first .. (inside the image);
+// rows whose bit is set in `fin` are final in the cycle: add their step and
+// previous norm (FP64) and keep them as the next cycle's x_prev.
+template <int SP>
+__device__ __forceinline__ void store_rows(const PersistArgs &A, const float *xs, int r_first,
+                                           int n, unsigned long long fin, int tid, int NC,
+                                           double &d2, double &n2)
+{
+    const int q4 = A.pitch / 4;
+    const int rows = min(n, A.H - r_first);
+    if (rows <= 0) return;
+    float4 *dst = reinterpret_cast<float4 *>(A.x + (size_t)r_first * A.pitch);
+    const float4 *src = reinterpret_cast<const float4 *>(xs);
+    const int n4 = rows * q4;
+    for (int i = tid; i < n4; i += NC) {
+        const int rr = i / q4, c4i = i - rr * q4;
+        const float4 v = src[rr * (SP / 4) + c4i];
+        dst[i] = v;
+        const int c4 = c4i * 4;
+        if (((fin >> rr) & 1ull) && c4 < A.W) {
+            float4 *pp = reinterpret_cast<float4 *>(A.xprev + (size_t)(r_first + rr) * A.pitch) + c4i;
+            const float4 pv = __ldcg(pp);
+            const float xv[4] = {v.x, v.y, v.z, v.w};
+            const float pw[4] = {pv.x, pv.y, pv.z, pv.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                if (c4 + e < A.W) {
+                    const double dd = (double)xv[e] - (double)pw[e];
+                    d2 = fma(dd, dd, d2);
+                    n2 = fma((double)pw[e], (double)pw[e], n2);
+                }
+            *pp = v;
+        }
+    }
+}
+
+// Shared-memory rows 1 .. n-1 move to 0 .. n-2.  Each thread owns whole
+// float4 columns and walks them top-down, so no other thread's data is read.
+template <int SP>
+__device__ __forceinline__ void shift_rows_up(const PersistArgs &A, float *xs, int n, int tid,
+                                              int NC)
+{
+    const int q4 = A.pitch / 4;
+    float4 *x4 = reinterpret_cast<float4 *>(xs);
+    for (int c = tid; c < q4; c += NC)
+        for (int k = 0; k + 1 < n; ++k) x4[k * (SP / 4) + c] = x4[(k + 1) * (SP / 4) + c];
 }
 
 enum { kGo = 0, kStop = 1, kAbort = 2 };
@@ -397,18 +471,29 @@ __global__ void __launch_bounds__(kPersistThreads, 1) persist_kernel(const Persi
     const int cta = blockIdx.x, G = gridDim.x;
     const int pitch = A.pitch;
 
-    const int4 seg = A.cta_sched[cta];
-    const int ntask = seg.y, npass = seg.z, ndep = seg.w;
+    // this CTA's schedule into shared memory
     {
-        const int4 *src = reinterpret_cast<const int4 *>(A.sched + seg.x);
+        const int *hdr = reinterpret_cast<const int *>(A.sched + A.cta_off[cta]);
+        const int nsd = hdr[0], ngr = hdr[1], npa = hdr[2], nde = hdr[3];
+        const int n16 = (int)((16 + sizeof(SideS) * nsd + sizeof(GrpS) * ngr +
+                               sizeof(long long) * npa + sizeof(int) * nde + 15) / 16);
+        const int4 *src = reinterpret_cast<const int4 *>(hdr);
         int4 *dst = reinterpret_cast<int4 *>(tbl);
-        const int n16 = (int)((sizeof(TaskS) * ntask + sizeof(long long) * npass +
-                               sizeof(int) * ndep + 15) / 16);
         for (int i = tid; i < n16; i += blockDim.x) dst[i] = src[i];
     }
-    const TaskS *tasks_s = reinterpret_cast<const TaskS *>(tbl);
-    const long long *pass_qoff = reinterpret_cast<const long long *>(tasks_s + ntask);
-    const int *deps_s = reinterpret_cast<const int *>(pass_qoff + npass);
+    __syncthreads();
+    const int nside = reinterpret_cast<const int *>(tbl)[0];
+    const int ngrp = reinterpret_cast<const int *>(tbl)[1];
+    const int npass_tab = reinterpret_cast<const int *>(tbl)[2];
+    const SideS *sides_s = reinterpret_cast<const SideS *>(tbl + 16);
+    const GrpS *grps_s = reinterpret_cast<const GrpS *>(sides_s + nside);
+    const long long *pass_qoff = reinterpret_cast<const long long *>(grps_s + ngrp);
+    const int *deps_s = reinterpret_cast<const int *>(pass_qoff + npass_tab);
+    // passes per cycle that carry increments (offsets with units present)
+    int npass = 0;
+    for (int si = 0; si < nside; ++si)
+        for (int a = 0; a < sides_s[si].L; ++a)
+            if (grps_s[sides_s[si].grp0 + a].U > 0) npass += sides_s[si].L;
 
     if (tid == 0) {
         for (int s = 0; s < S; ++s) {
@@ -431,30 +516,45 @@ __global__ void __launch_bounds__(kPersistThreads, 1) persist_kernel(const Persi
         for (int cyc = 0;; ++cyc) {
             const bool first = cyc == 0;
             if (lane == 0 && npass > 0 && !dead) {
-                auto provide = [&](int task, int b, int stg) {
+                // cursor over the passes of the cycle: (side, offset, pass)
+                struct Cur { int si, a, b; };
+                auto advance = [&](Cur &c) {
+                    if (++c.b < sides_s[c.si].L) return;
+                    c.b = 0;
+                    for (;;) {
+                        if (++c.a >= sides_s[c.si].L) { c.a = 0; if (++c.si >= nside) return; }
+                        if (grps_s[sides_s[c.si].grp0 + c.a].U > 0) return;
+                    }
+                };
+                auto provide = [&](const Cur &c, int stg) {
                     s_prov[stg] += 1;
-                    const TaskS &ts = tasks_s[task];
+                    const SideS &sd = sides_s[c.si];
+                    const int L = sd.L, U = grps_s[sd.grp0 + c.a].U;
                     const unsigned row_bytes = (unsigned)(pitch * sizeof(float));
-                    mbar_arrive_expect_tx(&full[stg], row_bytes * ts.L * ts.U);
+                    mbar_arrive_expect_tx(&full[stg], row_bytes * L * U);
                     // the first cycle starts from q = 0: copy from a zeroed block
-                    const float *src = first ? A.zeros : A.q + pass_qoff[ts.pass0 + b];
+                    const float *src = first ? A.zeros : A.q + pass_qoff[sd.pass0 + c.a * L + c.b];
                     float *dst = stage0 + (size_t)stg * A.stage_floats;
                     if (pitch == SP) {         // one contiguous block per unit
-                        for (int j = 0; j < ts.U; ++j)
-                            bulk_load(dst + (size_t)j * ts.L * SP,
-                                      first ? src : src + (size_t)j * ts.L * pitch,
-                                      row_bytes * ts.L, &full[stg]);
+                        for (int j = 0; j < U; ++j)
+                            bulk_load(dst + (size_t)j * L * SP,
+                                      first ? src : src + (size_t)j * L * pitch, row_bytes * L,
+                                      &full[stg]);
                     } else {                   // row by row into SP-strided rows
-                        for (int r = 0; r < ts.L * ts.U; ++r)
+                        for (int r = 0; r < L * U; ++r)
                             bulk_load(dst + (size_t)r * SP, first ? src : src + (size_t)r * pitch,
                                       row_bytes, &full[stg]);
                     }
                 };
-                int rt = 0, rb = 0, rs = s_head;       // refill cursor
+                Cur rc{0, 0, 0};               // refill cursor: first offset with units
+                while (rc.si < nside && grps_s[sides_s[rc.si].grp0 + rc.a].U == 0) {
+                    if (++rc.a >= sides_s[rc.si].L) { rc.a = 0; ++rc.si; }
+                }
+                int rs = s_head;
                 const int pre = npass < S ? npass : S;
                 for (int k = 0; k < pre; ++k) {
-                    provide(rt, rb, rs);
-                    if (++rb == tasks_s[rt].L) { rb = 0; ++rt; }
+                    provide(rc, rs);
+                    advance(rc);
                     rs = rs + 1 == S ? 0 : rs + 1;
                 }
                 for (int p = 0; p < npass; ++p) {
@@ -465,8 +565,8 @@ __global__ void __launch_bounds__(kPersistThreads, 1) persist_kernel(const Persi
                     }
                     wph ^= 1u << s_head;
                     if (p + S < npass) {
-                        provide(rt, rb, s_head);
-                        if (++rb == tasks_s[rt].L) { rb = 0; ++rt; }
+                        provide(rc, s_head);
+                        advance(rc);
                     }
                     s_head = s_head + 1 == S ? 0 : s_head + 1;
                 }
@@ -502,73 +602,55 @@ __global__ void __launch_bounds__(kPersistThreads, 1) persist_kernel(const Persi
 
     for (int cyc = 0;; ++cyc) {
         const bool first = cyc == 0;
-        for (int ti = 0; ti < ntask && !aborted; ++ti) {
-            const TaskS ts = tasks_s[ti];
-            const int L = ts.L, U = ts.U;
-            const int rows = U * L;
+        for (int si = 0; si < nside && !aborted; ++si) {
+            const SideS sd = sides_s[si];
+            const int L = sd.L, band = sd.U * L;
 
-            // wait for the other CTAs' tasks that last touched these rows
+            // side start: wait for the last publishers (other CTAs) of the rows
+            // this side may read, then bring the band in
             if (tid == 0) {
                 bool ok = true;
-                if (A.selftest_timeout && cta == 0 && ti == 0)
+                if (A.selftest_timeout && cta == 0 && si == 0)
                     ok = wait_geq(A, A.selftest_flag, 1u);   // a flag nothing sets
-                for (int k = 0; k < ts.dep_count && ok; ++k)
-                    ok = wait_geq(A, A.flags + deps_s[ts.dep_begin + k], (unsigned)(cyc + 1));
+                for (int k = 0; k < sd.dep_count && ok; ++k)
+                    ok = wait_geq(A, A.flags + deps_s[sd.dep_begin + k], (unsigned)(cyc + 1));
                 s_abort = ok ? 0 : 1;
             }
             consumers_sync(NC);
             if (s_abort) { aborted = true; break; }
-
-            // x rows of the task into shared memory (from L2)
-            {
-                const int q4 = pitch / 4;
-                const float4 *src = reinterpret_cast<const float4 *>(A.x + (size_t)ts.r_first * pitch);
-                float4 *dst = reinterpret_cast<float4 *>(xs);
-                const int n4 = rows * q4;
-                for (int i = tid; i < n4; i += NC) {
-                    const int rr = i / q4, c4 = i - rr * q4;
-                    dst[rr * (SP / 4) + c4] = __ldcg(src + i);
-                }
-            }
+            load_rows<SP>(A, xs, 0, sd.r0, band, tid, NC);
             consumers_sync(NC);
 
-            {
-                const bool ab = run_task_passes<SP>(cx, ts, s_cur, fph);
-                if (consumers_sync_or(ab, NC)) aborted = true;   // xs complete for the store
-            }
-            if (aborted) break;
-
-            // x back to L2; fused cycle norm on the rows this task touches last
-            {
-                const int q4 = pitch / 4;
-                const int n4 = rows * q4;
-                float4 *dst = reinterpret_cast<float4 *>(A.x + (size_t)ts.r_first * pitch);
-                const float4 *src = reinterpret_cast<const float4 *>(xs);
-                for (int i = tid; i < n4; i += NC) {
-                    const int rs = i / q4;
-                    const float4 v = src[rs * (SP / 4) + (i - rs * q4)];
-                    dst[i] = v;
-                    const int rr = i / q4;
-                    const int c4 = (i - rr * q4) * 4;
-                    if (((ts.final_mask >> rr) & 1ull) && c4 < A.W) {
-                        float4 *pp = reinterpret_cast<float4 *>(A.xprev + (size_t)(ts.r_first + rr) * pitch) + (i - rr * q4);
-                        const float4 pv = __ldcg(pp);
-                        const float xv[4] = {v.x, v.y, v.z, v.w};
-                        const float pw[4] = {pv.x, pv.y, pv.z, pv.w};
-#pragma unroll
-                        for (int e = 0; e < 4; ++e)
-                            if (c4 + e < A.W) {
-                                const double dd = (double)xv[e] - (double)pw[e];
-                                d2 = fma(dd, dd, d2);
-                                n2 = fma((double)pw[e], (double)pw[e], n2);
-                            }
-                        *pp = v;
+            for (int a = 0; a < L; ++a) {
+                const GrpS gp = grps_s[sd.grp0 + a];
+                if (a > 0) {
+                    // the band slides down one row: drop the (published) top row,
+                    // take the lower neighbour's published top row at the bottom
+                    shift_rows_up<SP>(A, xs, band, tid, NC);
+                    if (tid == 0) {
+                        const bool ok = gp.nb_flag < 0 ||
+                                        wait_geq(A, A.flags + gp.nb_flag, (unsigned)(cyc + 1));
+                        s_abort = ok ? 0 : 1;
                     }
+                    consumers_sync(NC);
+                    if (s_abort) { aborted = true; break; }
+                    load_rows<SP>(A, xs, band - 1, sd.r0 + a - 1 + band, 1, tid, NC);
+                    consumers_sync(NC);
                 }
+                if (gp.U > 0) {
+                    const PassTask pt{L, gp.U, sd.pass0 + a * L, sd.cS, sd.sqrt_cS, sd.cS64};
+                    const bool ab = run_task_passes<SP>(cx, pt, s_cur, fph);
+                    if (consumers_sync_or(ab, NC)) { aborted = true; break; }
+                }
+                // publish: the top row (dropped next), or the whole band at the end
+                const int nrows = a < L - 1 ? 1 : band;
+                const unsigned long long fin = a < L - 1 ? (unsigned long long)((sd.top_final >> a) & 1u)
+                                                         : sd.end_final;
+                store_rows<SP>(A, xs, sd.r0 + a, nrows, fin, tid, NC, d2, n2);
+                consumers_sync(NC);
+                if (tid == 0)   // release: the rows stored above (ordered by the barrier)
+                    st_release(A.flags + sd.flag0 + a, (unsigned)(cyc + 1));
             }
-            consumers_sync(NC);
-            if (tid == 0)   // release: the CTA's x stores (ordered by the barrier) before the flag
-                st_release(A.flags + ts.gid, (unsigned)(cyc + 1));
         }
 
         // ---- end of cycle: publish norms, grid barrier, same decision everywhere
