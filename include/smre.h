@@ -98,6 +98,9 @@ typedef struct {
     int maxstat_draws;          /* Monte Carlo draws for MAXSTAT (0: 1000)         */
     unsigned long long seed;    /* seed of the MAXSTAT draws                        */
     int flags;                  /* SMRE_F_* */
+    int max_ctas;               /* persistent launch: at most this many CTAs (one per
+                                   SM; 0 = all SMs), so that several projections can
+                                   run side by side on disjoint SMs                  */
 } smre_params;
 
 typedef struct {

@@ -61,6 +61,7 @@ class smre_params(ctypes.Structure):
         ("max_cycles", ctypes.c_int), ("tol", ctypes.c_double), ("tol_relative", ctypes.c_int),
         ("q_dtype", ctypes.c_int), ("icd_max_sweeps", ctypes.c_int),
         ("maxstat_draws", ctypes.c_int), ("seed", ctypes.c_ulonglong), ("flags", ctypes.c_int),
+        ("max_ctas", ctypes.c_int),
     ]
 
 
@@ -152,7 +153,8 @@ def _check(status, h=None, ok=(SMRE_OK,)):
 
 
 def make_params(H, W, sides, alpha=0.9, cmode=SMRE_C_PERSET, c_explicit=None, max_cycles=200,
-                tol=-1.0, tol_relative=False, icd_max_sweeps=0, maxstat_draws=0, seed=0, flags=0):
+                tol=-1.0, tol_relative=False, icd_max_sweeps=0, maxstat_draws=0, seed=0, flags=0,
+                max_ctas=0):
     """Build an ``smre_params`` (the arrays it points to are kept on the object)."""
     p = smre_params()
     sides_arr = (ctypes.c_int * len(sides))(*[int(s) for s in sides])
@@ -166,6 +168,7 @@ def make_params(H, W, sides, alpha=0.9, cmode=SMRE_C_PERSET, c_explicit=None, ma
     p.max_cycles, p.tol, p.tol_relative = int(max_cycles), float(tol), int(bool(tol_relative))
     p.q_dtype, p.icd_max_sweeps, p.maxstat_draws = 0, int(icd_max_sweeps), int(maxstat_draws)
     p.seed, p.flags = int(seed), int(flags)
+    p.max_ctas = int(max_ctas)
     p._sides_keep = sides_arr
     return p
 

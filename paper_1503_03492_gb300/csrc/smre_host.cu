@@ -28,6 +28,7 @@ struct smre_dykstra {
     int maxstat_draws = 1000;
     unsigned long long seed = 0;
     int flags = 0;
+    int max_ctas = 0;
     // stopping rule
     int max_cycles = 1;
     double tol = -1.0;
@@ -140,6 +141,7 @@ smre_status check_params(const smre_params *p, std::vector<int> &sides, std::vec
     if (std::isnan(p->tol)) return fail(nullptr, SMRE_EINVAL, "tol is NaN");
     if (p->icd_max_sweeps < 0 || p->maxstat_draws < 0)
         return fail(nullptr, SMRE_EINVAL, "negative sweep cap or draw count");
+    if (p->max_ctas < 0) return fail(nullptr, SMRE_EINVAL, "max_ctas is negative");
     return SMRE_OK;
 }
 
@@ -318,7 +320,8 @@ smre_status plan_persistent(smre_dykstra *h, int flags)
     const int H = h->H, W = h->W, pitch = h->pitch;
     const int sp = persist_smem_pitch(pitch);
     if (sp == 0) return SMRE_OK;
-    const int G = std::max(1, std::min(sms, H));
+    int G = std::max(1, std::min(sms, H));
+    if (h->max_ctas > 0) G = std::min(G, h->max_ctas);
 
     std::vector<int> sides_desc(h->sides.rbegin(), h->sides.rend());
     struct Side0 {
@@ -633,6 +636,7 @@ smre_status smre_dykstra_create(const smre_params *p, void *cuda_stream, smre_dy
     h->maxstat_draws = p->maxstat_draws ? p->maxstat_draws : 1000;
     h->seed = p->seed;
     h->flags = p->flags;
+    h->max_ctas = p->max_ctas;
     h->max_cycles = p->max_cycles;
     h->tol = p->tol;
     h->tol_relative = p->tol_relative ? 1 : 0;
