@@ -199,6 +199,102 @@ SMRE_API long long smre_dykstra_kernel_launches(const smre_dykstra *h);
 SMRE_API smre_status smre_dykstra_project_static(const smre_params *p, void *cuda_stream,
                                                  const float *x0, float *x, smre_result *res);
 
+/* ------------------------------------------------------------------------
+ * Batches: many images of different sizes projected together.
+ *
+ * The same standard method as smre_dykstra_project (Sec. 2.3, Algorithm 2,
+ * same set order, same per-window arithmetic), run over a batch of images at
+ * once: each cycle is one kernel launch per group (L, a) whose work list holds
+ * the window-rows of every image in the batch, then one norm and one
+ * stopping-test launch.  Every image keeps its own cycle count, stopping test
+ * and history, and its result does not depend on the other images in the
+ * batch (with FP32 increments it equals smre_dykstra_project's bit for bit).
+ *
+ * Increments may be stored in 16-bit types: q_s = sw * h with h in BF16 or
+ * FP16 and one power-of-two FP32 scale sw per window (x, sums and the test
+ * stay FP32; x = y - sw * h keeps x + sum_s q_s = x0 exact for the stored
+ * increments).  This halves the bytes the method moves and is an
+ * approximation: results differ from the FP32 path by the rounding of the
+ * stored increments (unit roundoff 2^-8 for BF16, 2^-11 for FP16).
+ *
+ * Images live in slots.  A batch owns one device arena (device_bytes) from
+ * which each admitted image takes its whole state: two images, the increments
+ * of all sum_L L^2 sets, their scales and small tables
+ * (smre_batch_image_bytes tells how much).  Work is stream-ordered on the
+ * stream given to smre_batch_create; a batch is not thread-safe.
+ * ---------------------------------------------------------------------- */
+typedef struct smre_batch smre_batch;
+
+#define SMRE_Q_FP32 0
+#define SMRE_Q_BF16 1
+#define SMRE_Q_FP16 2
+
+typedef struct {
+    const int *sides;           /* window sides, 1 <= L <= 16; duplicates ignored   */
+    int n_sides;
+    double alpha;               /* as smre_params (PERSET and CHI2)                 */
+    smre_cmode cmode;           /* PERSET, CHI2 or EXPLICIT (not MAXSTAT: its bound
+                                   depends on the image size)                       */
+    const double *c_explicit;   /* EXPLICIT: one bound per entry of sides           */
+    int max_cycles;             /* per-image cycle cap, >= 1                        */
+    double tol;                 /* per-image stopping tolerance; < 0: max_cycles    */
+    int tol_relative;           /* as smre_params                                   */
+    int q_dtype;                /* SMRE_Q_FP32, SMRE_Q_BF16 or SMRE_Q_FP16          */
+    int max_images;             /* slots, 1..65536                                  */
+    size_t device_bytes;        /* arena for the images' state                      */
+    int flags;                  /* reserved, 0                                      */
+} smre_batch_params;
+
+/* Arena bytes one height x width image takes under p (0: p invalid or the
+ * image unsupported: width above 2048 or a side above min(height, width)). */
+SMRE_API size_t smre_batch_image_bytes(const smre_batch_params *p, int height, int width);
+
+/* Validate p, compute the bounds and allocate the arena and the slot tables.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+SMRE_API smre_status smre_batch_create(const smre_batch_params *p, void *cuda_stream, smre_batch **out);
+
+/* Admit one image (x0: height x width floats, host or device, read before the
+ * call returns or in stream order) into a free slot: *slot receives its
+ * index, or -1 when no slot or not enough arena is free right now (status OK:
+ * retire finished images and try again).  Its cycles start with the next
+ * smre_batch_run, from q_s = 0.  Errors: EINVAL (size), ECUDA. */
+SMRE_API smre_status smre_batch_submit(smre_batch *b, int height, int width, const float *x0, int *slot);
+
+/* Enqueue `cycles` cycles for every admitted image that has not stopped
+ * (images that stop part-way skip the rest).  Returns once enqueued. */
+SMRE_API smre_status smre_batch_run(smre_batch *b, int cycles);
+
+/* Wait for the batch's stream, then report images that stopped since the
+ * last poll: up to max_done slot indices into done, the count into *n_done.
+ * Returns ETIMEOUT if a device-side wait expired (the batch stays usable). */
+SMRE_API smre_status smre_batch_poll(smre_batch *b, int *done, int max_done, int *n_done);
+
+/* Copy a stopped image's result into x (height x width, host or device; NULL
+ * to discard), fill *res (seconds = host time from submit to the poll that
+ * saw it stop), and free its slot and arena.  Returns the image's status
+ * (OK or ENOTCONVERGED), or EINVAL for a slot that is empty or not stopped. */
+SMRE_API smre_status smre_batch_retrieve(smre_batch *b, int slot, float *x, smre_result *res);
+
+/* Project n images together and wait: submit all (ENOMEM when they do not
+ * fit together), run until each stopped, retrieve all into x[i], res[i]. */
+SMRE_API smre_status smre_batch_project(smre_batch *b, int n, const int *heights, const int *widths,
+                                        const float *const *x0, float *const *x, smre_result *res);
+
+/* Images admitted and not yet retrieved. */
+SMRE_API int smre_batch_active(const smre_batch *b);
+
+/* Kernels the batch has launched since it was created. */
+SMRE_API long long smre_batch_kernel_launches(const smre_batch *b);
+
+/* Device bytes the batch holds (arena and tables). */
+SMRE_API size_t smre_batch_device_bytes(const smre_batch *b);
+
+/* Message of the last failure on b (NULL: of the last failed create on this thread). */
+SMRE_API const char *smre_batch_last_error(const smre_batch *b);
+
+/* Wait for the stream and free everything (NULL is allowed). */
+SMRE_API void smre_batch_destroy(smre_batch *b);
+
 /* Bytes of device memory the handle holds. */
 SMRE_API size_t smre_dykstra_device_bytes(const smre_dykstra *h);
 

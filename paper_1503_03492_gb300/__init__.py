@@ -26,6 +26,11 @@ __all__ = [
     "smre_dykstra_history", "smre_dykstra_icd_sweeps", "smre_dykstra_device_bytes",
     "smre_dykstra_destroy", "smre_last_error", "smre_version", "Projector", "EXPORTED",
     "smre_dykstra_kernel_launches", "make_params", "smre_dykstra_project_static",
+    "SMRE_Q_FP32", "SMRE_Q_BF16", "SMRE_Q_FP16", "smre_batch_params", "make_batch_params",
+    "smre_batch_image_bytes", "smre_batch_create", "smre_batch_submit", "smre_batch_run",
+    "smre_batch_poll", "smre_batch_retrieve", "smre_batch_project", "smre_batch_active",
+    "smre_batch_kernel_launches", "smre_batch_device_bytes", "smre_batch_last_error",
+    "smre_batch_destroy", "Batch",
 ]
 
 SMRE_OK, SMRE_EINVAL, SMRE_ENOMEM, SMRE_ECUDA, SMRE_ETIMEOUT, SMRE_ENOTCONVERGED = range(6)
@@ -33,6 +38,7 @@ SMRE_C_PERSET, SMRE_C_CHI2, SMRE_C_MAXSTAT, SMRE_C_EXPLICIT = range(4)
 SMRE_F_VIOLATION = 1
 SMRE_F_GROUP_LAUNCHES = 2
 SMRE_F_SELFTEST_TIMEOUT = 4
+SMRE_Q_FP32, SMRE_Q_BF16, SMRE_Q_FP16 = range(3)
 
 _STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENOTCONVERGED"}
 
@@ -42,7 +48,10 @@ EXPORTED = (
     "smre_dykstra_project_incomplete", "smre_dykstra_set_stopping", "smre_dykstra_bounds",
     "smre_dykstra_history", "smre_dykstra_icd_sweeps", "smre_dykstra_device_bytes",
     "smre_dykstra_destroy", "smre_last_error", "smre_version", "smre_dykstra_kernel_launches",
-    "smre_dykstra_project_static",
+    "smre_dykstra_project_static", "smre_batch_image_bytes", "smre_batch_create",
+    "smre_batch_submit", "smre_batch_run", "smre_batch_poll", "smre_batch_retrieve",
+    "smre_batch_project", "smre_batch_active", "smre_batch_kernel_launches",
+    "smre_batch_device_bytes", "smre_batch_last_error", "smre_batch_destroy",
 )
 
 
@@ -62,6 +71,17 @@ class smre_params(ctypes.Structure):
         ("q_dtype", ctypes.c_int), ("icd_max_sweeps", ctypes.c_int),
         ("maxstat_draws", ctypes.c_int), ("seed", ctypes.c_ulonglong), ("flags", ctypes.c_int),
         ("max_ctas", ctypes.c_int),
+    ]
+
+
+class smre_batch_params(ctypes.Structure):
+    _fields_ = [
+        ("sides", ctypes.POINTER(ctypes.c_int)), ("n_sides", ctypes.c_int),
+        ("alpha", ctypes.c_double), ("cmode", ctypes.c_int),
+        ("c_explicit", ctypes.POINTER(ctypes.c_double)),
+        ("max_cycles", ctypes.c_int), ("tol", ctypes.c_double), ("tol_relative", ctypes.c_int),
+        ("q_dtype", ctypes.c_int), ("max_images", ctypes.c_int),
+        ("device_bytes", ctypes.c_size_t), ("flags", ctypes.c_int),
     ]
 
 
@@ -114,6 +134,21 @@ def load():
         "smre_dykstra_project_static": (st, [P(smre_params), ctypes.c_void_p, ctypes.c_void_p,
                                              ctypes.c_void_p, P(smre_result)]),
         "smre_dykstra_destroy": (None, [H]),
+        "smre_batch_image_bytes": (ctypes.c_size_t, [P(smre_batch_params), ctypes.c_int,
+                                                     ctypes.c_int]),
+        "smre_batch_create": (st, [P(smre_batch_params), ctypes.c_void_p, P(H)]),
+        "smre_batch_submit": (st, [H, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                   P(ctypes.c_int)]),
+        "smre_batch_run": (st, [H, ctypes.c_int]),
+        "smre_batch_poll": (st, [H, P(ctypes.c_int), ctypes.c_int, P(ctypes.c_int)]),
+        "smre_batch_retrieve": (st, [H, ctypes.c_int, ctypes.c_void_p, P(smre_result)]),
+        "smre_batch_project": (st, [H, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_int),
+                                    P(ctypes.c_void_p), P(ctypes.c_void_p), P(smre_result)]),
+        "smre_batch_active": (ctypes.c_int, [H]),
+        "smre_batch_kernel_launches": (ctypes.c_longlong, [H]),
+        "smre_batch_device_bytes": (ctypes.c_size_t, [H]),
+        "smre_batch_last_error": (ctypes.c_char_p, [H]),
+        "smre_batch_destroy": (None, [H]),
         "smre_last_error": (ctypes.c_char_p, [H]),
         "smre_version": (ctypes.c_char_p, []),
     }
@@ -317,6 +352,161 @@ class Projector:
         if self.h:
             smre_dykstra_destroy(self.h)
             self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ batches
+
+def make_batch_params(sides, alpha=0.9, cmode=SMRE_C_PERSET, c_explicit=None, max_cycles=200,
+                      tol=-1.0, tol_relative=False, q_dtype=SMRE_Q_FP32, max_images=64,
+                      device_bytes=1 << 30, flags=0):
+    """Build an ``smre_batch_params`` (the arrays it points to are kept on the object)."""
+    p = smre_batch_params()
+    sides_arr = (ctypes.c_int * len(sides))(*[int(s) for s in sides])
+    p.sides, p.n_sides = sides_arr, len(sides)
+    p.alpha, p.cmode = float(alpha), int(cmode)
+    if c_explicit is not None:
+        c_arr = (ctypes.c_double * len(c_explicit))(*[float(c) for c in c_explicit])
+        p.c_explicit = c_arr
+        p._c_keep = c_arr
+    p.max_cycles, p.tol, p.tol_relative = int(max_cycles), float(tol), int(bool(tol_relative))
+    p.q_dtype, p.max_images, p.device_bytes = int(q_dtype), int(max_images), int(device_bytes)
+    p.flags = int(flags)
+    p._sides_keep = sides_arr
+    return p
+
+
+def _bcheck(status, b=None, ok=(SMRE_OK,)):
+    if status not in ok:
+        msg = load().smre_batch_last_error(b)
+        raise SmreError(status, msg.decode() if msg else "")
+    return status
+
+
+def smre_batch_image_bytes(params: smre_batch_params, H, W) -> int:
+    return int(load().smre_batch_image_bytes(ctypes.byref(params), int(H), int(W)))
+
+
+def smre_batch_create(params: smre_batch_params, stream=None):
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    b = ctypes.c_void_p()
+    _bcheck(load().smre_batch_create(ctypes.byref(params), ctypes.c_void_p(stream or 0),
+                                     ctypes.byref(b)))
+    return b.value
+
+
+def smre_batch_submit(b, x0) -> int:
+    """Admit x0 (H x W); returns its slot, or -1 when there is no room now."""
+    p0, k0 = _ptr(x0)
+    H, W = x0.shape
+    slot = ctypes.c_int(-1)
+    _bcheck(load().smre_batch_submit(b, int(H), int(W), p0, ctypes.byref(slot)), b)
+    return slot.value
+
+
+def smre_batch_run(b, cycles):
+    _bcheck(load().smre_batch_run(b, int(cycles)), b)
+
+
+def smre_batch_poll(b, max_done=4096):
+    done = (ctypes.c_int * max_done)()
+    n = ctypes.c_int()
+    _bcheck(load().smre_batch_poll(b, done, max_done, ctypes.byref(n)), b)
+    return [done[i] for i in range(n.value)]
+
+
+def smre_batch_retrieve(b, slot, x=None):
+    res = smre_result()
+    px, kx = _ptr(x) if x is not None else (None, None)
+    _bcheck(load().smre_batch_retrieve(b, int(slot), px, ctypes.byref(res)), b,
+            ok=(SMRE_OK, SMRE_ENOTCONVERGED))
+    return res
+
+
+def smre_batch_project(b, x0s, xs):
+    n = len(x0s)
+    keep = [_ptr(a) for a in x0s] + [_ptr(a) for a in xs]
+    Hs = (ctypes.c_int * n)(*[int(a.shape[0]) for a in x0s])
+    Ws = (ctypes.c_int * n)(*[int(a.shape[1]) for a in x0s])
+    p0 = (ctypes.c_void_p * n)(*[k[0] for k in keep[:n]])
+    p1 = (ctypes.c_void_p * n)(*[k[0] for k in keep[n:]])
+    res = (smre_result * n)()
+    _bcheck(load().smre_batch_project(b, n, Hs, Ws, p0, p1, res), b,
+            ok=(SMRE_OK, SMRE_ENOTCONVERGED))
+    return list(res)
+
+
+def smre_batch_active(b) -> int:
+    return int(load().smre_batch_active(b))
+
+
+def smre_batch_kernel_launches(b) -> int:
+    return int(load().smre_batch_kernel_launches(b))
+
+
+def smre_batch_device_bytes(b) -> int:
+    return int(load().smre_batch_device_bytes(b))
+
+
+def smre_batch_last_error(b=None) -> str:
+    m = load().smre_batch_last_error(b)
+    return m.decode() if m else ""
+
+
+def smre_batch_destroy(b):
+    load().smre_batch_destroy(b)
+
+
+class Batch:
+    """RAII wrapper over a batch: ``with Batch(sides, ...) as B: B.project([x0...], [x...])``."""
+
+    def __init__(self, sides, stream=None, **kw):
+        self.params = make_batch_params(sides, **kw)
+        self.b = smre_batch_create(self.params, stream)
+
+    def image_bytes(self, H, W):
+        return smre_batch_image_bytes(self.params, H, W)
+
+    def project(self, x0s, xs):
+        return smre_batch_project(self.b, x0s, xs)
+
+    def submit(self, x0):
+        return smre_batch_submit(self.b, x0)
+
+    def run(self, cycles):
+        smre_batch_run(self.b, cycles)
+
+    def poll(self):
+        return smre_batch_poll(self.b)
+
+    def retrieve(self, slot, x=None):
+        return smre_batch_retrieve(self.b, slot, x)
+
+    def active(self):
+        return smre_batch_active(self.b)
+
+    def kernel_launches(self):
+        return smre_batch_kernel_launches(self.b)
+
+    def device_bytes(self):
+        return smre_batch_device_bytes(self.b)
+
+    def close(self):
+        if self.b:
+            smre_batch_destroy(self.b)
+            self.b = None
 
     def __enter__(self):
         return self

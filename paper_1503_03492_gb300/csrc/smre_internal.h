@@ -63,19 +63,6 @@ constexpr int kMaxItems = 4;          // (unit, window chunk) items per consumer
 // items a consumer warp may hold in one task of side L (register budget)
 __host__ __device__ constexpr int max_items_for_side(int L) { return L <= 4 ? 4 : (L <= 8 ? 2 : 1); }
 
-// Task = the units of one group owned by one CTA (a contiguous row band).
-struct TaskDesc {
-    int g;                // group index in the cycle order
-    int ub, ue;           // unit range [ub, ue)
-    int dep_begin, dep_count;   // flags (task ids) to wait for, in deps[]
-};
-
-struct GroupDesc {
-    int L, a, tiling0;
-    float cS;
-    double cS64;
-};
-
 // Per-CTA schedule, kept in shared memory for the whole launch: one entry per
 // side the CTA takes part in (cycle order), then per offset a of that side a
 // GrpS, then the q offsets of every pass (a-major, b minor), then flag ids.
@@ -126,6 +113,75 @@ struct PersistArgs {
     int selftest_timeout;
     const unsigned *selftest_flag;
 };
+
+// ---- batched path (smre_batch.cu): many images, one launch per group step
+
+constexpr int kBatchConsumers = 480;   // consumer threads of the step kernel (15 warps + 1
+                                       // producer: 4 warps per SM sub-partition)
+constexpr int kBatchDescs = 8;         // ring descriptors (chunks in flight)
+constexpr int kBatchMaxWidth = 2048;   // widest image of the batched path
+constexpr int kBatchMaxSide = 16;      // largest window side of the batched path
+constexpr int kBatchNormRows = 16;     // rows per norm chunk (fixed: per-image order)
+
+// Per-image state of a batch slot (device memory).
+struct BImage {
+    float *x;                 // H x pitch work image
+    float *xprev;             // previous iterate (cycle norm)
+    void *q;                  // increment planes, element type of the batch
+    float *qs;                // per-window scales of the planes (BF16/FP16 only)
+    const long long *qoff;    // [n_planes] element offset of plane p in q
+    const long long *soff;    // [n_planes] float offset of plane p in qs
+    Control *ctl;
+    double *hist;             // [2 * hist_cap] step and |x_prev| per cycle
+    double *part;             // [2 * nchunks] norm partials of the current cycle
+    int H, W, pitch, nchunks;
+    int hist_cap, pad_;
+};
+
+// One launch of the step kernel: every item of group (L, a) over the batch.
+// An item is k consecutive units (k L rows) of one image, k * pitch <= the
+// kernel's virtual width.
+struct BStepArgs {
+    const BImage *imgs;
+    const int *active;        // [n_active] slot of each active image
+    const int *prefix;        // [n_active + 1] first item of each active image
+    const int *kpack;         // [n_active] units per item
+    int n_active, n_items;
+    int L, a, p0;             // side, row offset, plane of tiling (L, a, 0)
+    float cS, sqrt_cS;
+    double cS64;
+    int ring_bytes;           // shared-memory ring for x and increment blocks
+    int ring_offset;          // its offset in dynamic shared memory
+    unsigned long long timeout_ns;
+    int *err;                 // SMRE_ETIMEOUT is recorded here
+};
+
+struct BNormArgs {
+    const BImage *imgs;
+    const int *active;
+    const int *prefix;        // [n_active + 1] first norm chunk of each active image
+    int n_active, n_chunks;
+};
+
+struct BDecideArgs {
+    const BImage *imgs;
+    const int *active;
+    int n_active;
+    int max_cycles;
+    double tol;
+    int tol_relative;
+};
+
+// q element type of a batch: 0 FP32, 1 BF16, 2 FP16
+int batch_lb(int L);                       // register bucket of side L (1, 2, 4, 8, 12, 16)
+int batch_virtual_width(int L);            // columns one item may span
+size_t batch_part_bytes(int L);            // shared memory of the window sums
+int batch_threads();
+cudaError_t batch_prepare(int qtype, size_t smem_max);
+cudaError_t launch_batch_step(int qtype, const BStepArgs &A, int grid, size_t smem,
+                              cudaStream_t s);
+cudaError_t launch_batch_norm(const BNormArgs &A, int grid, cudaStream_t s);
+cudaError_t launch_batch_decide(const BDecideArgs &A, cudaStream_t s);
 
 bool persist_supported(int max_side);
 // shared-memory row stride (power of two >= pitch, 128..1024) or 0 if too wide

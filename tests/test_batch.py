@@ -1,0 +1,230 @@
+"""Batched projections (smre_batch_*) against the FP64 oracle and the
+single-image path.
+
+With FP32 increments a batch runs the same per-window arithmetic in the same
+set order as smre_dykstra_project, so every image must equal the single-image
+result bit for bit, and the oracle to the FP32 bar (max-abs relative 1e-5).
+An image's result must not depend on the other images in the batch or on
+when it joined.  BF16 / FP16 increments are an approximation whose error
+against the oracle is measured and bounded here.
+"""
+import os
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+NTH = os.cpu_count() or 1
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    return torch
+
+
+@pytest.fixture(scope="module")
+def smre(torch_cuda):
+    import paper_1503_03492_gb300 as m
+    return m
+
+
+def f32(x):
+    return np.ascontiguousarray(x, np.float32)
+
+
+def err(a, ref):
+    return float(np.abs(np.asarray(a, np.float64) - ref).max() / max(np.abs(ref).max(), 1e-300))
+
+
+def images(shapes, seed0=7):
+    from synthetic import blobs_residual
+    return [f32(blobs_residual(H, W, n_blobs=max(1, H * W // 700), seed=seed0 + 31 * i))
+            for i, (H, W) in enumerate(shapes)]
+
+
+def single(smre, torch, x0, sides, cS, cycles, flags):
+    H, W = x0.shape
+    with smre.Projector(H, W, sides, cmode=smre.SMRE_C_EXPLICIT, c_explicit=list(cS),
+                        max_cycles=cycles, tol=-1.0, flags=flags) as P:
+        xd = torch.from_numpy(x0).cuda()
+        out = torch.empty_like(xd)
+        P.project(xd, out)
+        return out.cpu().numpy()
+
+
+SHAPE_SETS = {
+    "small-sides": ([1, 2, 3, 5], [(37, 53), (64, 64), (19, 300), (70, 33), (5, 1029), (9, 2048),
+                                   (128, 96), (6, 7)]),
+    "sides-1-8": (list(range(1, 9)), [(64, 64), (40, 200), (97, 31), (8, 8), (33, 517)]),
+    "large-sides": ([9, 12, 16], [(16, 16), (40, 2048), (50, 77), (31, 130)]),
+}
+
+
+@pytest.mark.parametrize("case", list(SHAPE_SETS))
+def test_fp32_batch_equals_single_path_and_oracle(smre, torch_cuda, oracle_mod, case):
+    sides, shapes = SHAPE_SETS[case]
+    x0s = images(shapes)
+    cS = oracle_mod.bounds(sides, 0.9)
+    cycles = 3
+    outs = [np.full_like(x, np.nan) for x in x0s]
+    with smre.Batch(sides, cmode=smre.SMRE_C_EXPLICIT, c_explicit=list(cS), max_cycles=cycles,
+                    tol=-1.0, max_images=len(x0s), device_bytes=256 << 20) as B:
+        res = B.project(x0s, outs)
+        assert B.active() == 0
+    for x0, out, r in zip(x0s, outs, res):
+        assert r.cycles == cycles and r.status == smre.SMRE_OK
+        ref = oracle_mod.dykstra(x0.astype(np.float64), sides, cS, max_cycles=cycles, tol=-1,
+                                 n_threads=NTH).x
+        e = err(out, ref)
+        assert e <= TOL, (x0.shape, e)
+        for flags in (0, smre.SMRE_F_GROUP_LAUNCHES):
+            one = single(smre, torch_cuda, x0, sides, cS, cycles, flags)
+            assert np.array_equal(one, out), (x0.shape, flags, np.abs(one - out).max())
+
+
+def test_device_images_and_per_image_stopping(smre, torch_cuda, oracle_mod):
+    """Images stop at their own cycle (relative step test); each matches the
+    oracle run for the same number of cycles."""
+    torch = torch_cuda
+    sides = [1, 2, 4]
+    shapes = [(64, 64), (48, 80), (100, 40)]
+    x0s = images(shapes, seed0=101)
+    cS = oracle_mod.bounds(sides, 0.9)
+    xd = [torch.from_numpy(x).cuda() for x in x0s]
+    outs = [torch.empty_like(x) for x in xd]
+    with smre.Batch(sides, cmode=smre.SMRE_C_EXPLICIT, c_explicit=list(cS), max_cycles=400,
+                    tol=1e-4, tol_relative=True, max_images=4, device_bytes=64 << 20) as B:
+        res = B.project(xd, outs)
+    cyc = [r.cycles for r in res]
+    assert all(r.status == smre.SMRE_OK for r in res)
+    assert len(set(cyc)) > 1, cyc          # the images stopped at different cycles
+    for x0, out, r in zip(x0s, outs, res):
+        assert r.rel_step <= 1e-4 * (1 + 1e-6)
+        ref = oracle_mod.dykstra(x0.astype(np.float64), sides, cS, max_cycles=r.cycles, tol=-1,
+                                 n_threads=NTH).x
+        assert err(out.cpu().numpy(), ref) <= TOL
+
+
+def test_result_is_the_same_alone_and_in_the_mix(smre, torch_cuda, oracle_mod):
+    """An image joining a running batch between cycles gives the same bits as
+    the same image alone (continuous batching)."""
+    sides = list(range(1, 6))
+    cS = oracle_mod.bounds(sides, 0.9)
+    kw = dict(cmode=smre.SMRE_C_EXPLICIT, c_explicit=list(cS), max_cycles=60, tol=1e-5,
+              tol_relative=True, max_images=8, device_bytes=128 << 20)
+    a, b, c, d = images([(72, 90), (130, 64), (33, 257), (64, 64)], seed0=211)
+    alone = np.full_like(a, np.nan)
+    with smre.Batch(sides, **kw) as B:
+        (ra,) = B.project([a], [alone])
+    with smre.Batch(sides, **kw) as B:
+        sb, sc = B.submit(b), B.submit(c)
+        B.run(3)
+        sa = B.submit(a)           # joins while b and c are mid-way
+        B.run(2)
+        sd = B.submit(d)
+        assert min(sa, sb, sc, sd) >= 0
+        by_slot = {sa: a, sb: b, sc: c, sd: d}
+        got = {}
+        for _ in range(200):
+            B.run(4)
+            for s in B.poll():
+                out = np.full(by_slot[s].shape, np.nan, np.float32)
+                got[s] = (B.retrieve(s, out), out)
+            if len(got) == 4:
+                break
+        assert len(got) == 4
+    rm, mixed = got[sa]
+    assert rm.cycles == ra.cycles
+    assert np.array_equal(mixed, alone)
+    ref = oracle_mod.dykstra(a.astype(np.float64), sides, cS, max_cycles=ra.cycles, tol=-1,
+                             n_threads=NTH).x
+    assert err(alone, ref) <= TOL
+
+
+# unit roundoff of the stored increments: BF16 keeps 8 significant bits, FP16 11
+U16 = {1: 2.0 ** -8, 2: 2.0 ** -11}
+
+
+@pytest.mark.parametrize("qdt", [1, 2])
+def test_mixed_precision_error_against_oracle(smre, torch_cuda, oracle_mod, qdt):
+    """16-bit increments: each stored increment carries a relative rounding
+    error of at most the type's unit roundoff u, and |q_s| <= |x0 - x|, so the
+    error against the FP64 oracle stays within 2 u of max |x| (max-abs
+    relative); the FP32 path of the same batch stays within 1e-5."""
+    bound = 2 * U16[qdt]
+    sides = list(range(1, 9))
+    cS = oracle_mod.bounds(sides, 0.9)
+    (x0, y0) = images([(96, 128), (64, 200)], seed0=307)
+    out = [np.full_like(x0, np.nan), np.full_like(y0, np.nan)]
+    out32 = [np.full_like(x0, np.nan), np.full_like(y0, np.nan)]
+    kw = dict(cmode=smre.SMRE_C_EXPLICIT, c_explicit=list(cS), max_cycles=20, tol=-1.0,
+              max_images=2, device_bytes=128 << 20)
+    with smre.Batch(sides, q_dtype=qdt, **kw) as B:
+        B.project([x0, y0], out)
+    with smre.Batch(sides, q_dtype=smre.SMRE_Q_FP32, **kw) as B:
+        B.project([x0, y0], out32)
+    for x, o, o32 in zip((x0, y0), out, out32):
+        ref = oracle_mod.dykstra(x.astype(np.float64), sides, cS, max_cycles=20, tol=-1,
+                                 n_threads=NTH).x
+        e, e32 = err(o, ref), err(o32, ref)
+        print(f"q_dtype {qdt} {x.shape}: err vs oracle {e:.3e} (FP32 path {e32:.3e})")
+        assert e32 <= TOL
+        assert np.isfinite(o).all() and e <= bound, e
+
+
+def test_admission_by_memory_and_slots(smre, torch_cuda):
+    sides = [1, 2]
+    x = images([(64, 64)])[0]
+    p = smre.make_batch_params(sides, max_cycles=5, max_images=3)
+    one = smre.smre_batch_image_bytes(p, 64, 64)
+    assert one > 0
+    with smre.Batch(sides, max_cycles=5, tol=-1.0, max_images=3, device_bytes=2 * one + 1024) as B:
+        s0, s1 = B.submit(x), B.submit(x)
+        assert s0 >= 0 and s1 >= 0 and s0 != s1
+        assert B.submit(x) == -1                 # arena full: admission waits
+        B.run(5)
+        done = B.poll()
+        assert sorted(done) == sorted([s0, s1])
+        out = np.empty_like(x)
+        B.retrieve(s0, out)
+        s2 = B.submit(x)                          # the freed bytes admit the next one
+        assert s2 >= 0
+        B.retrieve(s1)
+        B.run(5)
+        assert B.poll() == [s2]
+        out2 = np.empty_like(x)
+        B.retrieve(s2, out2)
+        assert np.array_equal(out, out2)
+        assert B.active() == 0
+    with smre.Batch(sides, max_cycles=5, max_images=1, device_bytes=8 << 20) as B:
+        assert B.submit(x) >= 0
+        assert B.submit(x) == -1                 # no free slot
+
+
+def test_batch_argument_errors(smre, torch_cuda):
+    with pytest.raises(smre.SmreError) as e:
+        smre.Batch([17], max_images=1, device_bytes=1 << 20)
+    assert e.value.status == smre.SMRE_EINVAL
+    with pytest.raises(smre.SmreError):
+        smre.Batch([1, 2], cmode=smre.SMRE_C_MAXSTAT, max_images=1, device_bytes=1 << 20)
+    with pytest.raises(smre.SmreError):
+        smre.Batch([1, 2], q_dtype=3, max_images=1, device_bytes=1 << 20)
+    with smre.Batch([1, 2, 4], max_cycles=3, max_images=2, device_bytes=64 << 20) as B:
+        with pytest.raises(smre.SmreError) as e:
+            B.submit(np.zeros((8, 2049), np.float32))
+        assert e.value.status == smre.SMRE_EINVAL
+        with pytest.raises(smre.SmreError):
+            B.submit(np.zeros((3, 100), np.float32))          # side 4 > height
+        s = B.submit(np.ones((16, 16), np.float32))
+        with pytest.raises(smre.SmreError):
+            B.retrieve(s)                                     # not run yet
+        B.run(3)
+        assert B.poll() == [s]
+        r = B.retrieve(s)
+        assert r.cycles == 3
