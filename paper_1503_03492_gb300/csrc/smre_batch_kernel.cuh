@@ -1,0 +1,656 @@
+// Batched standard Dykstra path on sm_103a: the images of a batch (any mix of
+// sizes up to 2048 columns) share every launch.
+//
+// Paper: Sec. 2.3 (Algorithm 2, projection Eq. dykstra:if) with the increment
+// update of the Sec. 3.2 listing, applied set by set in the order sides
+// descending, row offset a, column offset b.
+//
+// One cycle is one launch of the step kernel per group (L, a) -- the L
+// tilings (L, a, b) share their window-rows ("units"), so a CTA that holds a
+// unit runs its L passes b = 0..L-1 back to back -- followed by one launch of
+// the norm kernel and one of the decide kernel.  Units of one group are
+// disjoint, in one image and across images, so the step kernel treats the
+// whole batch as one list of items: an item is k consecutive units of one
+// image (k * pitch <= the kernel's virtual width), CTAs take items
+// blockIdx.x, blockIdx.x + gridDim.x, ...
+//
+// Inside a CTA a producer warp streams each item's blocks -- the k L rows of
+// x, then the increment block of every pass (and, for BF16/FP16 increments,
+// the per-window scales) -- into a byte ring of shared memory with bulk
+// asynchronous copies (TMA engine), as far ahead as the ring allows.  The 704
+// consumer threads keep the item's x in registers (thread t owns columns
+// t + 704 j), form y = x + q, the column sums of y^2 and, through shared
+// memory, the window sums in a fixed column order (the same order as the
+// single-image kernels, so FP32 results agree bit for bit), take the ball
+// test and write x (at the item's end) and the new increments straight to
+// HBM.
+//
+// Mixed precision (BF16 / FP16 increments): each window's increment block is
+// stored as q_s = sw * h with h in the 16-bit type and sw a power of two per
+// window (FP32, in a scale plane beside the increments) chosen from the
+// window's increment norm (1 - scale) sqrt(t) >= max |q_i|, so |h| <= 2^15
+// fits FP16.  The update is consistent: x = y - sw * h, so x + sum_s q_s = x0
+// holds for the stored increments up to FP32 rounding.
+//
+// Every wait has a time limit; on expiry the kernel records SMRE_ETIMEOUT,
+// lets its copies in flight land and returns.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "smre_internal.h"
+#include "smre_ptx.cuh"
+
+namespace smre {
+
+namespace batch {
+
+constexpr float kNearBand = 1e-6f;   // FP64 recheck band of the ball test, relative to cS
+constexpr int kNC = kBatchConsumers;
+constexpr int kNCW = kNC / 32;
+constexpr int kD = kBatchDescs;
+constexpr int kThreads = kNC + 64;   // consumers, producer warp, storer warp
+constexpr int kNormThreads = 256;
+
+// Element type of the stored increments: pairs of adjacent columns are
+// loaded and stored together (8 bytes for FP32, 4 for BF16 / FP16); store2
+// returns the stored values converted back to FP32 (before any scale).
+template <typename QT>
+struct QConv;
+template <>
+struct QConv<float> {
+    static constexpr bool mixed = false;
+    __device__ static float2 load2(const float *p) { return *reinterpret_cast<const float2 *>(p); }
+    __device__ static float2 store2(float *p, float a, float b)
+    {
+        *reinterpret_cast<float2 *>(p) = make_float2(a, b);
+        return make_float2(a, b);
+    }
+};
+template <>
+struct QConv<__nv_bfloat16> {
+    static constexpr bool mixed = true;
+    __device__ static float2 load2(const __nv_bfloat16 *p)
+    {
+        return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p));
+    }
+    __device__ static float2 store2(__nv_bfloat16 *p, float a, float b)
+    {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        *reinterpret_cast<__nv_bfloat162 *>(p) = h;
+        return __bfloat1622float2(h);
+    }
+};
+template <>
+struct QConv<__half> {
+    static constexpr bool mixed = true;
+    __device__ static float2 load2(const __half *p)
+    {
+        return __half22float2(*reinterpret_cast<const __half2 *>(p));
+    }
+    __device__ static float2 store2(__half *p, float a, float b)
+    {
+        const __half2 h = __floats2half2_rn(a, b);
+        *reinterpret_cast<__half2 *>(p) = h;
+        return __half22float2(h);
+    }
+};
+
+// Kernels are built for each side L <= 12 (compile-time L: the row loops
+// unroll with fixed offsets) and once for sides 13..16 (run-time L <= 16).
+__host__ __device__ constexpr int lb_of(int L) { return L <= 12 ? L : 16; }
+// column pairs per consumer thread: x of an item takes 2 LB CPP registers
+__host__ __device__ constexpr int cpp_of(int LB) { return LB == 1 ? 4 : LB == 2 ? 3 : 2; }
+constexpr int kOutside = -(1 << 24);   // window index of a column outside the item
+__host__ __device__ constexpr int vw_of(int LB) { return 2 * kNC * cpp_of(LB); }
+__host__ __device__ constexpr int round16(int v) { return (v + 15) & ~15; }
+__host__ __device__ constexpr int round128(int v) { return (v + 127) & ~127; }
+// scale-plane row length of side L (windows per unit row, padded to 16 bytes)
+__host__ __device__ constexpr int scale_row(int W, int L) { return ((W / L) + 3) & ~3; }
+
+struct BItem {
+    int slot, u0, nu;
+};
+
+// 2^(k + shift) for the smallest k with v <= 2^k (exponent k in ex), read from
+// the bits of v; 0 when v is zero, subnormal, not finite, or the power would
+// leave the normal range (increments that small are stored as zero).
+__device__ __forceinline__ float pow2_above(float v, int shift, int &ex)
+{
+    const unsigned u = __float_as_uint(v);
+    const int be = (int)((u >> 23) & 0xffu);
+    ex = be - 127 + ((u & 0x7fffffu) != 0u);   // v <= 2^ex
+    const int r = ex + shift + 127;
+    if (!(v > 0.f) || be == 0 || be == 255 || r < 1 || r > 254) return 0.f;
+    return __uint_as_float((unsigned)r << 23);
+}
+
+__device__ __forceinline__ int find_active(const int *prefix, int n_active, int item)
+{
+    // last active index i with prefix[i] <= item (images without items are skipped)
+    int lo = 0, hi = n_active;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(prefix + mid) <= item) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ BItem decode_item(const BStepArgs &A, int item)
+{
+    const int i = find_active(A.prefix, A.n_active, item);
+    BItem it;
+    it.slot = __ldg(A.active + i);
+    const int k = __ldg(A.kpack + i);
+    const int units = (A.imgs[it.slot].H - A.a) / A.L;
+    it.u0 = (item - __ldg(A.prefix + i)) * k;
+    it.nu = min(k, units - it.u0);
+    return it;
+}
+
+// Bounded wait for an mbarrier phase.  On expiry (or when another CTA or
+// role gave up) it records the time-out, raises the CTA's abort flag and
+// returns false.
+__device__ inline bool wait_phase(uint64_t *bar, unsigned parity, const BStepArgs &A,
+                           volatile int *s_abort)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer();
+    for (;;) {
+        if (mbar_try_wait_sleep(bar, parity, 20000u)) return true;
+        if (*s_abort || ld_volatile(A.err)) break;
+        if (globaltimer() - t0 > A.timeout_ns) {
+            atomicCAS(A.err, 0, (int)SMRE_ETIMEOUT);
+            break;
+        }
+    }
+    *s_abort = 1;
+    return false;
+}
+
+// Producer: walks the CTA's items in the consumers' order and fills the ring
+// with, per item, the x block and one increment block per pass.  In an
+// image's first cycle the increments are zero: their blocks are only space
+// for the consumers' results, nothing is read.
+template <typename QT>
+__device__ void produce(const BStepArgs &A, unsigned char *ring, uint64_t *full,
+                        uint64_t *written, int *s_off, volatile int *s_abort)
+{
+    constexpr bool MIXED = QConv<QT>::mixed;
+    const int L = A.L;
+    int head = 0, d_next = 0, d_tail = 0, n_out = 0;
+    unsigned wph = 0;    // parity of the next `written` wait, per descriptor
+    unsigned fiss = 0;   // toggled per issue: parity of the latest `full` phase, per descriptor
+    bool dead = false;
+
+    auto pop = [&]() -> bool {   // the oldest chunk was released
+        if (!wait_phase(&written[d_tail], (wph >> d_tail) & 1u, A, s_abort)) return false;
+        wph ^= 1u << d_tail;
+        d_tail = d_tail + 1 == kD ? 0 : d_tail + 1;
+        --n_out;
+        return true;
+    };
+    // place n bytes in the ring: the free space runs from head to the start
+    // of the oldest chunk still held, wrapping to 0 when the end is too close
+    auto alloc = [&](int n, int &at) -> bool {
+        for (;;) {
+            if (n_out == 0) {
+                at = 0;
+                return true;
+            }
+            if (n_out < kD) {
+                const int tail = s_off[d_tail];
+                if (head > tail) {
+                    if (head + n <= A.ring_bytes) { at = head; return true; }
+                    if (n <= tail) { at = 0; return true; }
+                } else if (head + n <= tail) {
+                    at = head;
+                    return true;
+                }
+            }
+            if (!pop()) return false;
+        }
+    };
+    // one chunk of n bytes; b0 (+ b1) bytes copied from src0 (and src1) when load
+    auto issue = [&](int n, bool load, const void *src0, unsigned b0, const void *src1,
+                     unsigned b1) -> bool {
+        int at;
+        if (!alloc(round128(n), at)) return false;
+        s_off[d_next] = at;
+        if (load) {
+            mbar_arrive_expect_tx(&full[d_next], b0 + b1);
+            bulk_load(ring + at, src0, b0, &full[d_next]);
+            if (b1) bulk_load(ring + at + round16((int)b0), src1, b1, &full[d_next]);
+        } else {
+            mbar_arrive(&full[d_next]);
+        }
+        fiss ^= 1u << d_next;
+        head = at + round128(n);
+        ++n_out;
+        d_next = d_next + 1 == kD ? 0 : d_next + 1;
+        return true;
+    };
+
+    for (int item = blockIdx.x; item < A.n_items && !dead; item += gridDim.x) {
+        const BItem it = decode_item(A, item);
+        const BImage im = A.imgs[it.slot];
+        if (im.ctl->stop) continue;
+        const int P = im.pitch;
+        const bool first = im.ctl->cycles == 0;
+        const unsigned xbytes = (unsigned)(it.nu * L * P) * 4u;
+        if (!issue((int)xbytes, true, im.x + (size_t)(A.a + L * it.u0) * P, xbytes, nullptr, 0)) {
+            dead = true;
+            break;
+        }
+        const unsigned qbytes = (unsigned)(it.nu * L * P) * (unsigned)sizeof(QT);
+        const int nwp = scale_row(im.W, L);
+        const unsigned sbytes = MIXED ? (unsigned)(it.nu * nwp) * 4u : 0u;
+        for (int b = 0; b < L; ++b) {
+            const QT *qsrc = reinterpret_cast<const QT *>(im.q) + im.qoff[A.p0 + b] +
+                             (size_t)it.u0 * L * P;
+            const float *ssrc = MIXED ? im.qs + im.soff[A.p0 + b] + (size_t)it.u0 * nwp : nullptr;
+            if (!issue(round16((int)qbytes) + (int)sbytes, !first, qsrc, qbytes, ssrc, sbytes)) {
+                dead = true;
+                break;
+            }
+        }
+    }
+    if (!dead) {
+        while (n_out > 0)
+            if (!pop()) { dead = true; break; }
+    }
+    if (dead) {
+        // let every copy in flight land before the shared memory is released
+        for (int k = 0, d = d_tail; k < n_out; ++k, d = d + 1 == kD ? 0 : d + 1) {
+            const unsigned par = ((fiss >> d) & 1u) ^ 1u;
+            for (unsigned it = 0; !mbar_try_wait(&full[d], par) && it < (1u << 22); ++it) {
+            }
+        }
+    }
+}
+
+// Storer: once the consumers have written a pass's new increments (and
+// scales) into its chunk, copies the chunk to the increment plane with bulk
+// stores and releases it to the producer when the copy has read it.
+template <typename QT>
+__device__ void store_back(const BStepArgs &A, unsigned char *ring, uint64_t *written,
+                           uint64_t *ready, const int *s_off, volatile int *s_abort)
+{
+    constexpr bool MIXED = QConv<QT>::mixed;
+    const int L = A.L;
+    int ds = 0;
+    unsigned rph = 0;   // parity of the next `ready` wait, per descriptor
+    for (int item = blockIdx.x; item < A.n_items; item += gridDim.x) {
+        const BItem it = decode_item(A, item);
+        const BImage im = A.imgs[it.slot];
+        if (im.ctl->stop) continue;
+        const int P = im.pitch;
+        const int nwp = scale_row(im.W, L);
+        const unsigned qbytes = (unsigned)(it.nu * L * P) * (unsigned)sizeof(QT);
+        const unsigned sbytes = MIXED ? (unsigned)(it.nu * nwp) * 4u : 0u;
+        ds = ds + 1 == kD ? 0 : ds + 1;   // the x chunk: released by the consumers
+        for (int b = 0; b < L; ++b) {
+            if (!wait_phase(&ready[ds], (rph >> ds) & 1u, A, s_abort)) {
+                bulk_wait_all();
+                return;
+            }
+            rph ^= 1u << ds;
+            const unsigned char *src = ring + s_off[ds];
+            bulk_store(reinterpret_cast<QT *>(im.q) + im.qoff[A.p0 + b] + (size_t)it.u0 * L * P,
+                       src, qbytes);
+            if (MIXED)
+                bulk_store(im.qs + im.soff[A.p0 + b] + (size_t)it.u0 * nwp, src + round16((int)qbytes),
+                           sbytes);
+            bulk_commit();
+            bulk_wait_read0();
+            mbar_arrive_cnt(&written[ds], kNCW);
+            ds = ds + 1 == kD ? 0 : ds + 1;
+        }
+    }
+    bulk_wait_all();
+}
+
+template <typename QT, int LB, bool EXACT>
+__global__ void __launch_bounds__(kThreads, 1) bstep_kernel(const BStepArgs A)
+{
+    using C = QConv<QT>;
+    constexpr bool MIXED = C::mixed;
+    constexpr int CPP = cpp_of(LB);
+    constexpr int VW = vw_of(LB);
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem);   // [kD] chunk landed
+    uint64_t *written = full + kD;                          // [kD] chunk free again
+    uint64_t *ready = written + kD;                         // [kD] new increments in the chunk
+    int *s_off = reinterpret_cast<int *>(ready + kD);       // [kD] ring offset of each chunk
+    float *part = reinterpret_cast<float *>(smem + 256);    // [VW] column sums of y^2
+    float *wsum = part + VW;                                // [VW] window sums, at the first column
+    double *part64 = reinterpret_cast<double *>(wsum + VW); // [VW] FP64 recheck
+    unsigned char *ring = smem + A.ring_offset;
+    __shared__ volatile int s_abort;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int L = EXACT ? LB : A.L;
+    if (tid == 0) {
+        for (int d = 0; d < kD; ++d) {
+            mbar_init(&full[d], 1);
+            mbar_init(&written[d], kNCW);
+            mbar_init(&ready[d], kNCW);
+            s_off[d] = 0;
+        }
+        fence_mbar_init();
+        s_abort = 0;
+    }
+    __syncthreads();
+
+    if (warp == kNCW) {
+        if (lane == 0) produce<QT>(A, ring, full, written, s_off, &s_abort);
+        return;
+    }
+    if (warp == kNCW + 1) {
+        if (lane == 0) store_back<QT>(A, ring, written, ready, s_off, &s_abort);
+        return;
+    }
+
+    // ------------------------------------------------------------ consumers
+    int dc = 0;          // descriptor of the next chunk
+    unsigned fph = 0;    // parity of the next `full` wait, per descriptor
+    const float cS = A.cS, sqrt_cS = A.sqrt_cS;
+    for (int item = blockIdx.x; item < A.n_items; item += gridDim.x) {
+        const BItem it = decode_item(A, item);
+        const BImage im = A.imgs[it.slot];
+        if (im.ctl->stop) continue;
+        const int P = im.pitch, W = im.W;
+        const bool first = im.ctl->cycles == 0;
+        const int nwp = scale_row(W, L);
+        // Thread t owns the column pairs (c, c + 1), c = 2 (t + kNC j) mod P of
+        // unit sj of the item.  o: row-0 offset of the pair in a chunk; po: its
+        // column-sum slot; so: its unit's scale row; (vv, rr): window of column
+        // c in the current pass and c's place in it, advanced each pass.
+        // Columns outside the item get a window index that never lies in a pass.
+        int o[CPP], po[CPP], so[CPP], vv[CPP], rr[CPP];
+#pragma unroll
+        for (int j = 0; j < CPP; ++j) {
+            const int vc = 2 * (tid + kNC * j);
+            const int sj = vc / P;
+            const int c = vc - sj * P;
+            o[j] = sj * L * P + c;
+            po[j] = sj * P + c;
+            so[j] = sj * nwp;
+            vv[j] = sj < it.nu && c < W ? c / L : kOutside;
+            rr[j] = c % L;
+        }
+
+        // the item's rows of x into registers
+        float x[LB][CPP][2];
+        bool bad = !wait_phase(&full[dc], (fph >> dc) & 1u, A, &s_abort);
+        fph ^= 1u << dc;
+        {
+            const float *xb = reinterpret_cast<const float *>(ring + s_off[dc]);
+#pragma unroll
+            for (int j = 0; j < CPP; ++j)
+#pragma unroll
+                for (int i = 0; i < LB; ++i) {
+                    float2 v = make_float2(0.f, 0.f);
+                    if (i < L && vv[j] >= 0 && !bad)
+                        v = *reinterpret_cast<const float2 *>(xb + o[j] + i * P);
+                    x[i][j][0] = v.x;
+                    x[i][j][1] = v.y;
+                }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&written[dc]);
+        dc = dc + 1 == kD ? 0 : dc + 1;
+
+        bool aborted = false;
+        for (int b = 0; b < L; ++b) {
+            const int nv = (W - b) / L;   // windows per unit row in this pass
+            if (!bad) bad = !wait_phase(&full[dc], (fph >> dc) & 1u, A, &s_abort);
+            fph ^= 1u << dc;
+            unsigned char *chunk = ring + s_off[dc];
+            QT *qc = reinterpret_cast<QT *>(chunk);   // qc[o + i P]: row i of the pair
+            float *sc = reinterpret_cast<float *>(chunk + round16(it.nu * L * P * (int)sizeof(QT)));
+            // windows of both columns of each pair
+            int w1[CPP], r1[CPP];
+            bool on[CPP][2];
+#pragma unroll
+            for (int j = 0; j < CPP; ++j) {
+                r1[j] = rr[j] + 1 == L ? 0 : rr[j] + 1;
+                w1[j] = rr[j] + 1 == L ? vv[j] + 1 : vv[j];
+                on[j][0] = vv[j] >= 0 && vv[j] < nv;
+                on[j][1] = w1[j] >= 0 && w1[j] < nv;
+            }
+            // y = x + q_s on the owned columns, and the column sums of y^2
+#pragma unroll
+            for (int j = 0; j < CPP; ++j) {
+                if (!(on[j][0] || on[j][1]) || bad) continue;
+                float s0 = 1.f, s1 = 1.f;
+                if (MIXED && !first) {
+                    s0 = on[j][0] ? sc[so[j] + vv[j]] : 0.f;
+                    s1 = on[j][1] ? sc[so[j] + w1[j]] : 0.f;
+                }
+                float sq0 = 0.f, sq1 = 0.f;
+#pragma unroll
+                for (int i = 0; i < LB; ++i) {
+                    if (i < L) {
+                        float2 qv = make_float2(0.f, 0.f);
+                        if (!first) {
+                            qv = C::load2(qc + o[j] + i * P);
+                            if (MIXED) {
+                                qv.x *= s0;
+                                qv.y *= s1;
+                            }
+                        }
+                        const float y0 = x[i][j][0] + qv.x, y1 = x[i][j][1] + qv.y;
+                        x[i][j][0] = y0;
+                        x[i][j][1] = y1;
+                        sq0 = fmaf(y0, y0, sq0);
+                        sq1 = fmaf(y1, y1, sq1);
+                    }
+                }
+                *reinterpret_cast<float2 *>(part + po[j]) = make_float2(sq0, sq1);
+            }
+            if (named_sync_or(1, bad, kNC)) {   // column sums complete (or a copy was lost)
+                aborted = true;
+                break;
+            }
+
+            // one thread per window (its first column) sums the L column sums in
+            // column order; windows within the band of the ball test are flagged
+            bool near = false;
+#pragma unroll
+            for (int j = 0; j < CPP; ++j)
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    if (!on[j][e] || (e ? r1[j] : rr[j]) != 0) continue;
+                    const float *pp = part + po[j] + e;
+                    float pv[LB];
+#pragma unroll
+                    for (int m = 0; m < LB; ++m) pv[m] = m < L ? pp[m] : 0.f;
+                    float ts = 0.f;
+#pragma unroll
+                    for (int m = 0; m < LB; ++m)
+                        if (m < L) ts += pv[m];
+                    wsum[po[j] + e] = ts;
+                    if (fabsf(ts - cS) <= kNearBand * cS) near = true;
+                }
+            const bool any_near = named_sync_or(1, near, kNC);
+
+            // the ball test of Eq. (dykstra:if) per owned column
+            float scale[CPP][2], tsv[CPP][2];
+#pragma unroll
+            for (int j = 0; j < CPP; ++j)
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    scale[j][e] = 1.f;
+                    tsv[j][e] = 0.f;
+                    if (!on[j][e]) continue;
+                    const float ts = wsum[po[j] + e - (e ? r1[j] : rr[j])];
+                    tsv[j][e] = ts;
+                    if (ts > cS) scale[j][e] = sqrt_cS * rsqrtf(ts);
+                }
+            if (any_near) {
+                // rare: windows within the band get their sums again in FP64
+#pragma unroll
+                for (int j = 0; j < CPP; ++j)
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        double s64 = 0.0;
+                        if (on[j][e]) {
+#pragma unroll
+                            for (int i = 0; i < LB; ++i)
+                                if (i < L) s64 = fma((double)x[i][j][e], (double)x[i][j][e], s64);
+                            part64[po[j] + e] = s64;
+                        }
+                    }
+                named_sync(1, kNC);
+#pragma unroll
+                for (int j = 0; j < CPP; ++j)
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        if (!on[j][e] || (e ? r1[j] : rr[j]) != 0) continue;
+                        if (fabsf(tsv[j][e] - cS) > kNearBand * cS) continue;
+                        double t64 = 0.0;
+                        for (int m = 0; m < L; ++m) t64 += part64[po[j] + e + m];
+                        part64[po[j] + e] = t64;   // the window's FP64 sum, at its first column
+                    }
+                named_sync(1, kNC);
+#pragma unroll
+                for (int j = 0; j < CPP; ++j)
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        if (!on[j][e] || fabsf(tsv[j][e] - cS) > kNearBand * cS) continue;
+                        const double t64 = part64[po[j] + e - (e ? r1[j] : rr[j])];
+                        scale[j][e] = t64 > A.cS64 ? (float)sqrt(A.cS64 / t64) : 1.f;
+                        tsv[j][e] = (float)t64;
+                    }
+            }
+
+            // x = p_s(y), q_s = y - x; the new increments go into the chunk,
+            // which the storer copies to the plane
+#pragma unroll
+            for (int j = 0; j < CPP; ++j) {
+                if (!(on[j][0] || on[j][1])) continue;
+                if (!MIXED) {
+#pragma unroll
+                    for (int i = 0; i < LB; ++i)
+                        if (i < L) {
+                            const float y0 = x[i][j][0], y1 = x[i][j][1];
+                            const float n0 = y0 * scale[j][0], n1 = y1 * scale[j][1];
+                            x[i][j][0] = n0;
+                            x[i][j][1] = n1;
+                            C::store2(qc + o[j] + i * P, y0 - n0, y1 - n1);
+                        }
+                } else {
+                    // window scale sw: a power of two with |q_i| / sw <= 2^15 (FP16
+                    // holds up to 65504), from |q_i| <= |q_s|_2 = (1 - scale) sqrt(t)
+                    float sw[2], inv[2];
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        sw[e] = 0.f;
+                        inv[e] = 0.f;
+                        if (on[j][e]) {
+                            const float t = tsv[j][e];
+                            const float qn = (1.f - scale[j][e]) * (t * rsqrtf(t));
+                            int ex;
+                            const float sw_e = pow2_above(qn, -14, ex);
+                            if (sw_e > 0.f) {
+                                sw[e] = sw_e;
+                                inv[e] = __uint_as_float((unsigned)(127 + 14 - ex) << 23);
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int i = 0; i < LB; ++i)
+                        if (i < L) {
+                            const float y0 = x[i][j][0], y1 = x[i][j][1];
+                            const float2 h = C::store2(qc + o[j] + i * P,
+                                                       (y0 - y0 * scale[j][0]) * inv[0],
+                                                       (y1 - y1 * scale[j][1]) * inv[1]);
+                            x[i][j][0] = y0 - h.x * sw[0];   // consistent: x = y - deq(q_s)
+                            x[i][j][1] = y1 - h.y * sw[1];
+                        }
+                    if (on[j][0] && rr[j] == 0) sc[so[j] + vv[j]] = sw[0];
+                    if (on[j][1] && r1[j] == 0) sc[so[j] + w1[j]] = sw[1];
+                }
+            }
+            fence_proxy_async_smem();   // the chunk's new contents, for the bulk store
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&ready[dc]);
+            dc = dc + 1 == kD ? 0 : dc + 1;
+#pragma unroll
+            for (int j = 0; j < CPP; ++j) {   // next pass: windows start one column later
+                if (--rr[j] < 0) {
+                    rr[j] += L;
+                    --vv[j];
+                }
+            }
+        }
+        if (aborted) break;
+        // the item's rows of x back to HBM (both columns of a pair; a column
+        // past the width lands in the row's padding)
+        float *xg = im.x + (size_t)(A.a + L * it.u0) * P;
+#pragma unroll
+        for (int j = 0; j < CPP; ++j)
+            if (vv[j] > kOutside + kBatchMaxSide) {
+#pragma unroll
+                for (int i = 0; i < LB; ++i)
+                    if (i < L)
+                        *reinterpret_cast<float2 *>(xg + o[j] + i * P) =
+                            make_float2(x[i][j][0], x[i][j][1]);
+            }
+    }
+}
+
+template <typename QT, int LB, bool EXACT>
+cudaError_t launch_step_t(const BStepArgs &A, int grid, size_t smem, cudaStream_t s)
+{
+    bstep_kernel<QT, LB, EXACT><<<grid, kThreads, smem, s>>>(A);
+    return cudaGetLastError();
+}
+
+template <typename QT>
+cudaError_t launch_step_q(const BStepArgs &A, int grid, size_t smem, cudaStream_t s)
+{
+    switch (A.L) {
+        case 1: return launch_step_t<QT, 1, true>(A, grid, smem, s);
+        case 2: return launch_step_t<QT, 2, true>(A, grid, smem, s);
+        case 3: return launch_step_t<QT, 3, true>(A, grid, smem, s);
+        case 4: return launch_step_t<QT, 4, true>(A, grid, smem, s);
+        case 5: return launch_step_t<QT, 5, true>(A, grid, smem, s);
+        case 6: return launch_step_t<QT, 6, true>(A, grid, smem, s);
+        case 7: return launch_step_t<QT, 7, true>(A, grid, smem, s);
+        case 8: return launch_step_t<QT, 8, true>(A, grid, smem, s);
+        case 9: return launch_step_t<QT, 9, true>(A, grid, smem, s);
+        case 10: return launch_step_t<QT, 10, true>(A, grid, smem, s);
+        case 11: return launch_step_t<QT, 11, true>(A, grid, smem, s);
+        case 12: return launch_step_t<QT, 12, true>(A, grid, smem, s);
+        default: return launch_step_t<QT, 16, false>(A, grid, smem, s);
+    }
+}
+
+template <typename QT>
+cudaError_t prepare_q(size_t smem)
+{
+    const void *ks[] = {
+        (const void *)bstep_kernel<QT, 1, true>,  (const void *)bstep_kernel<QT, 2, true>,
+        (const void *)bstep_kernel<QT, 3, true>,  (const void *)bstep_kernel<QT, 4, true>,
+        (const void *)bstep_kernel<QT, 5, true>,  (const void *)bstep_kernel<QT, 6, true>,
+        (const void *)bstep_kernel<QT, 7, true>,  (const void *)bstep_kernel<QT, 8, true>,
+        (const void *)bstep_kernel<QT, 9, true>,  (const void *)bstep_kernel<QT, 10, true>,
+        (const void *)bstep_kernel<QT, 11, true>, (const void *)bstep_kernel<QT, 12, true>,
+        (const void *)bstep_kernel<QT, 16, false>};
+    for (const void *k : ks) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace batch
+
+}  // namespace smre

@@ -116,8 +116,9 @@ struct PersistArgs {
 
 // ---- batched path (smre_batch.cu): many images, one launch per group step
 
-constexpr int kBatchConsumers = 480;   // consumer threads of the step kernel (15 warps + 1
-                                       // producer: 4 warps per SM sub-partition)
+constexpr int kBatchConsumers = 512;   // consumer threads of the step kernel (16 warps, plus
+                                       // a producer and a storer warp: at most 5 warps per
+                                       // SM sub-partition, 96 registers a thread)
 constexpr int kBatchDescs = 8;         // ring descriptors (chunks in flight)
 constexpr int kBatchMaxWidth = 2048;   // widest image of the batched path
 constexpr int kBatchMaxSide = 16;      // largest window side of the batched path
@@ -173,7 +174,7 @@ struct BDecideArgs {
 };
 
 // q element type of a batch: 0 FP32, 1 BF16, 2 FP16
-int batch_lb(int L);                       // register bucket of side L (1, 2, 4, 8, 12, 16)
+int batch_lb(int L);                       // kernel variant of side L (L itself up to 12, then 16)
 int batch_virtual_width(int L);            // columns one item may span
 size_t batch_part_bytes(int L);            // shared memory of the window sums
 int batch_threads();
@@ -181,6 +182,13 @@ cudaError_t batch_prepare(int qtype, size_t smem_max);
 cudaError_t launch_batch_step(int qtype, const BStepArgs &A, int grid, size_t smem,
                               cudaStream_t s);
 cudaError_t launch_batch_norm(const BNormArgs &A, int grid, cudaStream_t s);
+// per increment type (smre_batch_f32.cu, smre_batch_bf16.cu, smre_batch_f16.cu)
+cudaError_t launch_batch_step_f32(const BStepArgs &A, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_batch_step_bf16(const BStepArgs &A, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_batch_step_f16(const BStepArgs &A, int grid, size_t smem, cudaStream_t s);
+cudaError_t batch_prepare_f32(size_t smem);
+cudaError_t batch_prepare_bf16(size_t smem);
+cudaError_t batch_prepare_f16(size_t smem);
 cudaError_t launch_batch_decide(const BDecideArgs &A, cudaStream_t s);
 
 bool persist_supported(int max_side);
