@@ -81,6 +81,11 @@ typedef enum {
                                      so smre_dykstra_project must return
                                      SMRE_ETIMEOUT and the handle stay usable        */
 
+/* increment storage types (smre_params.q_dtype, smre_batch_params.q_dtype) */
+#define SMRE_Q_FP32 0
+#define SMRE_Q_BF16 1
+#define SMRE_Q_FP16 2
+
 typedef struct {
     int height, width;          /* pixels: 1 <= height <= 65535, 1 <= width <= 4096 */
     const int *sides;           /* n_sides window sides, 1 <= L <= min(H, W, 32);
@@ -93,7 +98,9 @@ typedef struct {
     double tol;                 /* stopping tolerance; < 0: run exactly max_cycles  */
     int tol_relative;           /* 0: |x_r - x_{r-1}|_2 <= tol;
                                    1: |x_r - x_{r-1}|_2 <= tol |x_{r-1}|_2         */
-    int q_dtype;                /* increment storage: 0 = FP32 (only value so far)  */
+    int q_dtype;                /* increment storage: SMRE_Q_FP32 (0), SMRE_Q_BF16 or
+                                   SMRE_Q_FP16 (16-bit values with a per-window scale,
+                                   see the batches below; width <= 2048, sides <= 16) */
     int icd_max_sweeps;         /* per-tile sweep cap of the incomplete method (0: 1000) */
     int maxstat_draws;          /* Monte Carlo draws for MAXSTAT (0: 1000)         */
     unsigned long long seed;    /* seed of the MAXSTAT draws                        */
@@ -122,8 +129,11 @@ SMRE_API smre_status smre_bounds(const smre_params *p, double *cS_out);
 
 /* Validate p, compute the bounds, and allocate every device buffer a
  * projection of an H x W image with these sides needs: the increments q_s of
- * all sets (sum over L of L^2 * H * W FP32 values, padded rows), two work
- * images and reduction scratch.  `cuda_stream` is a cudaStream_t (NULL: the
+ * all sets (sum over L of L^2 * H * W values, padded rows), two work images and
+ * reduction scratch.  With 16-bit increments, and for FP32 images wider than
+ * 1024 pixels (width <= 2048, sides <= 16, no SMRE_F_GROUP_LAUNCHES), the
+ * handle runs the standard method through a one-image batch (smre_batch_*
+ * below), which then holds the increments.  `cuda_stream` is a cudaStream_t (NULL: the
  * legacy default stream).  On success *out owns all of it.
  * Errors: EINVAL (bad parameters), ENOMEM, ECUDA. */
 SMRE_API smre_status smre_dykstra_create(const smre_params *p, void *cuda_stream, smre_dykstra **out);
@@ -224,10 +234,6 @@ SMRE_API smre_status smre_dykstra_project_static(const smre_params *p, void *cud
  * stream given to smre_batch_create; a batch is not thread-safe.
  * ---------------------------------------------------------------------- */
 typedef struct smre_batch smre_batch;
-
-#define SMRE_Q_FP32 0
-#define SMRE_Q_BF16 1
-#define SMRE_Q_FP16 2
 
 typedef struct {
     const int *sides;           /* window sides, 1 <= L <= 16; duplicates ignored   */

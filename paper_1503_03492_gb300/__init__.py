@@ -189,7 +189,7 @@ def _check(status, h=None, ok=(SMRE_OK,)):
 
 def make_params(H, W, sides, alpha=0.9, cmode=SMRE_C_PERSET, c_explicit=None, max_cycles=200,
                 tol=-1.0, tol_relative=False, icd_max_sweeps=0, maxstat_draws=0, seed=0, flags=0,
-                max_ctas=0):
+                max_ctas=0, q_dtype=0):
     """Build an ``smre_params`` (the arrays it points to are kept on the object)."""
     p = smre_params()
     sides_arr = (ctypes.c_int * len(sides))(*[int(s) for s in sides])
@@ -201,7 +201,7 @@ def make_params(H, W, sides, alpha=0.9, cmode=SMRE_C_PERSET, c_explicit=None, ma
         p.c_explicit = c_arr
         p._c_keep = c_arr
     p.max_cycles, p.tol, p.tol_relative = int(max_cycles), float(tol), int(bool(tol_relative))
-    p.q_dtype, p.icd_max_sweeps, p.maxstat_draws = 0, int(icd_max_sweeps), int(maxstat_draws)
+    p.q_dtype, p.icd_max_sweeps, p.maxstat_draws = int(q_dtype), int(icd_max_sweeps), int(maxstat_draws)
     p.seed, p.flags = int(seed), int(flags)
     p.max_ctas = int(max_ctas)
     p._sides_keep = sides_arr

@@ -406,6 +406,14 @@ smre_status smre_batch_create(const smre_batch_params *p, void *cuda_stream, smr
 
 smre_status smre_batch_submit(smre_batch *b, int height, int width, const float *x0, int *slot)
 {
+    return smre::batch_submit_ld(b, height, width, x0, width, slot);
+}
+
+}  // extern "C"
+
+smre_status smre::batch_submit_ld(smre_batch *b, int height, int width, const float *x0, int ld,
+                                  int *slot)
+{
     if (!b) return bfail(nullptr, SMRE_EINVAL, "batch is NULL");
     if (!slot || !x0) return bfail(b, SMRE_EINVAL, "x0 / slot is NULL");
     *slot = -1;
@@ -451,7 +459,7 @@ smre_status smre_batch_submit(smre_batch *b, int height, int width, const float 
     SUB_CK(cudaMemcpyAsync(base + lo.soff, lo.soff_tab.data(), sizeof(long long) * np,
                            cudaMemcpyHostToDevice, b->stream));
     SUB_CK(cudaMemcpyAsync(b->d_imgs + s, &im, sizeof(BImage), cudaMemcpyHostToDevice, b->stream));
-    SUB_CK(cudaMemcpy2DAsync(im.x, sizeof(float) * lo.pitch, x0, sizeof(float) * width,
+    SUB_CK(cudaMemcpy2DAsync(im.x, sizeof(float) * lo.pitch, x0, sizeof(float) * ld,
                              sizeof(float) * width, height, cudaMemcpyDefault, b->stream));
     SUB_CK(cudaMemcpy2DAsync(im.xprev, sizeof(float) * lo.pitch, im.x, sizeof(float) * lo.pitch,
                              sizeof(float) * width, height, cudaMemcpyDeviceToDevice, b->stream));
@@ -471,6 +479,8 @@ smre_status smre_batch_submit(smre_batch *b, int height, int width, const float 
     *slot = s;
     return SMRE_OK;
 }
+
+extern "C" {
 
 smre_status smre_batch_run(smre_batch *b, int cycles)
 {
@@ -544,13 +554,21 @@ smre_status smre_batch_poll(smre_batch *b, int *done, int max_done, int *n_done)
 
 smre_status smre_batch_retrieve(smre_batch *b, int slot, float *x, smre_result *res)
 {
+    const int ld = b && slot >= 0 && slot < b->max_images ? b->slots[slot].W : 0;
+    return smre::batch_retrieve_ld(b, slot, x, ld, res);
+}
+
+}  // extern "C"
+
+smre_status smre::batch_retrieve_ld(smre_batch *b, int slot, float *x, int ld, smre_result *res)
+{
     if (!b) return bfail(nullptr, SMRE_EINVAL, "batch is NULL");
     if (slot < 0 || slot >= b->max_images || !b->slots[slot].used)
         return bfail(b, SMRE_EINVAL, "slot %d holds no image", slot);
     auto &sl = b->slots[slot];
     if (!sl.done) return bfail(b, SMRE_EINVAL, "slot %d has not finished (poll first)", slot);
     if (x)
-        BCK(b, cudaMemcpy2DAsync(x, sizeof(float) * sl.W, sl.img.x, sizeof(float) * sl.img.pitch,
+        BCK(b, cudaMemcpy2DAsync(x, sizeof(float) * ld, sl.img.x, sizeof(float) * sl.img.pitch,
                                  sizeof(float) * sl.W, sl.H, cudaMemcpyDefault, b->stream));
     BCK(b, cudaStreamSynchronize(b->stream));
     const Control &c = b->h_ctl[slot];
@@ -572,6 +590,8 @@ smre_status smre_batch_retrieve(smre_batch *b, int slot, float *x, smre_result *
     b->dirty = true;
     return (smre_status)status;
 }
+
+extern "C" {
 
 smre_status smre_batch_project(smre_batch *b, int n, const int *heights, const int *widths,
                                const float *const *x0, float *const *x, smre_result *res)
@@ -641,3 +661,50 @@ const char *smre_batch_last_error(const smre_batch *b)
 void smre_batch_destroy(smre_batch *b) { free_batch(b); }
 
 }  // extern "C"
+
+namespace smre {
+
+smre_status batch_set_rule(smre_batch *b, int max_cycles, double tol, int tol_relative)
+{
+    if (max_cycles > b->hist_cap)
+        return bfail(b, SMRE_EINVAL, "max_cycles %d above the batch's history of %d", max_cycles,
+                     b->hist_cap);
+    b->max_cycles = max_cycles;
+    b->tol = tol;
+    b->tol_relative = tol_relative ? 1 : 0;
+    return SMRE_OK;
+}
+
+smre_status batch_run_one(smre_batch *b, int height, int width, const float *x0, float *x,
+                          int ld, double *hist, int hist_cap, Control *ctl_out)
+{
+    if (!b->active.empty()) return bfail(b, SMRE_EINVAL, "the batch already holds images");
+    int slot = -1;
+    smre_status st = batch_submit_ld(b, height, width, x0, ld, &slot);
+    if (st != SMRE_OK) return st;
+    if (slot < 0) return bfail(b, SMRE_ENOMEM, "image does not fit the batch arena");
+    int ran = 0, n_done = 0, done = -1;
+    while (n_done == 0) {
+        const int k = std::min(8, std::max(1, b->max_cycles - ran));
+        st = smre_batch_run(b, k);
+        if (st == SMRE_OK) st = smre_batch_poll(b, &done, 1, &n_done);
+        if (st != SMRE_OK) {
+            b->heap.release(b->slots[slot].off, b->slots[slot].bytes);
+            b->slots[slot].used = false;
+            b->active.clear();
+            b->dirty = true;
+            return st;
+        }
+        ran += k;
+    }
+    const Control c = b->h_ctl[slot];
+    if (ctl_out) *ctl_out = c;
+    const int n = std::min(c.cycles, std::min(hist_cap, b->hist_cap));
+    if (hist && n > 0)
+        BCK(b, cudaMemcpyAsync(hist, b->slots[slot].img.hist, sizeof(double) * 2 * n,
+                               cudaMemcpyDeviceToDevice, b->stream));
+    st = batch_retrieve_ld(b, slot, x, ld, nullptr);
+    return st == SMRE_ENOTCONVERGED ? SMRE_OK : st;
+}
+
+}  // namespace smre

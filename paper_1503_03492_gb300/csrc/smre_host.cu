@@ -29,6 +29,11 @@ struct smre_dykstra {
     unsigned long long seed = 0;
     int flags = 0;
     int max_ctas = 0;
+    int q_dtype = 0;
+    // a one-image batch runs the standard method instead of the handle's own
+    // kernels (16-bit increments, or FP32 images too wide for the persistent
+    // kernel); see use_batch
+    smre_batch *bat = nullptr;
     // stopping rule
     int max_cycles = 1;
     double tol = -1.0;
@@ -136,7 +141,12 @@ smre_status check_params(const smre_params *p, std::vector<int> &sides, std::vec
         return fail(nullptr, SMRE_EINVAL, "alpha %g outside (0, 1)", p->alpha);
     if ((int)p->cmode < 0 || (int)p->cmode > 3)
         return fail(nullptr, SMRE_EINVAL, "unknown cmode %d", (int)p->cmode);
-    if (p->q_dtype != 0) return fail(nullptr, SMRE_EINVAL, "q_dtype %d not supported", p->q_dtype);
+    if (p->q_dtype < SMRE_Q_FP32 || p->q_dtype > SMRE_Q_FP16)
+        return fail(nullptr, SMRE_EINVAL, "q_dtype %d unknown", p->q_dtype);
+    if (p->q_dtype != SMRE_Q_FP32 &&
+        (p->width > kBatchMaxWidth || sides.back() > kBatchMaxSide))
+        return fail(nullptr, SMRE_EINVAL, "16-bit increments need width <= %d and sides <= %d",
+                    kBatchMaxWidth, kBatchMaxSide);
     if (p->max_cycles < 1) return fail(nullptr, SMRE_EINVAL, "max_cycles must be >= 1");
     if (std::isnan(p->tol)) return fail(nullptr, SMRE_EINVAL, "tol is NaN");
     if (p->icd_max_sweeps < 0 || p->maxstat_draws < 0)
@@ -178,6 +188,40 @@ smre_status maxstat_q(const smre_params *p, const std::vector<int> &sides, doubl
     int idx = (int)std::ceil(p->alpha * draws) - 1;
     idx = std::max(0, std::min(draws - 1, idx));
     q_out = all[idx];
+    return SMRE_OK;
+}
+
+// Whether the handle projects through a one-image batch: always for 16-bit
+// increments (only the batched kernels store them), and for FP32 images
+// wider than the persistent kernel takes, where the batched step kernel beats
+// one launch per group (unless the caller asked for group launches).
+bool use_batch(const smre_params *p, int max_side)
+{
+    if (p->q_dtype != SMRE_Q_FP32) return true;
+    if (p->flags & SMRE_F_GROUP_LAUNCHES) return false;
+    return persist_smem_pitch(round_up(p->width, 32)) == 0 && p->width <= kBatchMaxWidth &&
+           max_side <= kBatchMaxSide;
+}
+
+smre_status make_handle_batch(smre_dykstra *h)
+{
+    if (h->bat) {
+        smre_batch_destroy(h->bat);
+        h->bat = nullptr;
+    }
+    smre_batch_params bp{};
+    bp.sides = h->sides.data();
+    bp.n_sides = (int)h->sides.size();
+    bp.cmode = SMRE_C_EXPLICIT;
+    bp.c_explicit = h->cS.data();
+    bp.max_cycles = h->max_cycles;
+    bp.tol = h->tol;
+    bp.tol_relative = h->tol_relative;
+    bp.q_dtype = h->q_dtype;
+    bp.max_images = 1;
+    bp.device_bytes = smre_batch_image_bytes(&bp, h->H, h->W) + 4096;
+    const smre_status st = smre_batch_create(&bp, h->stream, &h->bat);
+    if (st != SMRE_OK) return fail(h, st, "one-image batch: %s", smre_batch_last_error(nullptr));
     return SMRE_OK;
 }
 
@@ -637,6 +681,7 @@ smre_status smre_dykstra_create(const smre_params *p, void *cuda_stream, smre_dy
     h->seed = p->seed;
     h->flags = p->flags;
     h->max_ctas = p->max_ctas;
+    h->q_dtype = p->q_dtype;
     h->max_cycles = p->max_cycles;
     h->tol = p->tol;
     h->tol_relative = p->tol_relative ? 1 : 0;
@@ -650,6 +695,8 @@ smre_status smre_dykstra_create(const smre_params *p, void *cuda_stream, smre_dy
     }
     for (size_t i = 0; i < sides.size(); ++i) h->cS_of[sides[i]] = h->cS[i];
     build_schedule(h);
+    const bool batched = use_batch(p, sides.back());
+    if (batched) h->q_floats = 0;   // the batch holds the increments
 
     auto bail = [&](smre_status s2) {
         g_err = h->err;
@@ -683,7 +730,12 @@ smre_status smre_dykstra_create(const smre_params *p, void *cuda_stream, smre_dy
     h->dev_bytes = sizeof(float) * std::max<size_t>(h->q_floats, 1) + 2 * img +
                    sizeof(double) * 2 * h->n_partials + sizeof(Control) + sizeof(double);
     if (ensure_hist(h, h->max_cycles) != SMRE_OK) return bail(SMRE_ENOMEM);
-    if (plan_persistent(h, p->flags) != SMRE_OK) return bail(SMRE_ECUDA);
+    if (batched) {
+        st = make_handle_batch(h);
+        if (st != SMRE_OK) return bail(st);
+    } else if (plan_persistent(h, p->flags) != SMRE_OK) {
+        return bail(SMRE_ECUDA);
+    }
 #undef CKC
     *out = h;
     return SMRE_OK;
@@ -699,6 +751,8 @@ smre_status smre_dykstra_set_stopping(smre_dykstra *h, int max_cycles, double to
     h->max_cycles = max_cycles;
     h->tol = tol;
     h->tol_relative = tol_relative ? 1 : 0;
+    if (h->bat && batch_set_rule(h->bat, max_cycles, tol, tol_relative) != SMRE_OK)
+        return make_handle_batch(h);   // more cycles than its history holds: a new batch
     return SMRE_OK;
 }
 
@@ -714,7 +768,15 @@ smre_status smre_dykstra_project(smre_dykstra *h, const float *x0, float *x, smr
     CK(h, cudaEventRecord(h->ev0, h->stream));
 
     int cycles = 0;
-    if (h->persist) {
+    if (h->bat) {
+        const long long l0 = smre_batch_kernel_launches(h->bat);
+        Control c{};
+        st = batch_run_one(h->bat, h->H, h->W, h->xw, h->xw, h->pitch, h->hist, h->hist_cap, &c);
+        if (st != SMRE_OK) return fail(h, st, "%s", smre_batch_last_error(h->bat));
+        h->launches += smre_batch_kernel_launches(h->bat) - l0;
+        *h->ctl_host = c;
+        cycles = c.cycles;
+    } else if (h->persist) {
         st = run_persistent(h);
         if (st != SMRE_OK) return st;
         CK(h, cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(Control), cudaMemcpyDeviceToHost,
@@ -722,7 +784,7 @@ smre_status smre_dykstra_project(smre_dykstra *h, const float *x0, float *x, smr
         CK(h, cudaStreamSynchronize(h->stream));
         cycles = h->ctl_host->cycles;
     }
-    for (int cyc = 0; !h->persist && cyc < h->max_cycles; ++cyc) {
+    for (int cyc = 0; !h->persist && !h->bat && cyc < h->max_cycles; ++cyc) {
         for (const Group &g : h->groups) {
             GroupArgs A{};
             A.x = h->xw;
@@ -924,7 +986,10 @@ smre_status smre_dykstra_icd_sweeps(smre_dykstra *h, int *out, int n_max, int *n
     return SMRE_OK;
 }
 
-size_t smre_dykstra_device_bytes(const smre_dykstra *h) { return h ? h->dev_bytes : 0; }
+size_t smre_dykstra_device_bytes(const smre_dykstra *h)
+{
+    return h ? h->dev_bytes + smre_batch_device_bytes(h->bat) : 0;
+}
 
 long long smre_dykstra_kernel_launches(const smre_dykstra *h) { return h ? h->launches : 0; }
 
@@ -932,6 +997,7 @@ void smre_dykstra_destroy(smre_dykstra *h)
 {
     if (!h) return;
     if (h->stream || h->q) cudaStreamSynchronize(h->stream);
+    smre_batch_destroy(h->bat);
     cudaFree(h->q);
     cudaFree(h->xw);
     cudaFree(h->xprev);

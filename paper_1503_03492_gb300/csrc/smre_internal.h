@@ -191,6 +191,17 @@ cudaError_t batch_prepare_bf16(size_t smem);
 cudaError_t batch_prepare_f16(size_t smem);
 cudaError_t launch_batch_decide(const BDecideArgs &A, cudaStream_t s);
 
+// A batch serving one image for an smre_dykstra handle (smre_batch_host.cu):
+// change the stopping rule (max_cycles up to the history the batch was made
+// for), or project one device image and copy its history and control block.
+smre_status batch_set_rule(smre_batch *b, int max_cycles, double tol, int tol_relative);
+smre_status batch_run_one(smre_batch *b, int height, int width, const float *x0, float *x,
+                          int ld, double *hist, int hist_cap, Control *ctl_out);
+// submit / retrieve with a row stride of ld floats for the caller's image
+smre_status batch_submit_ld(smre_batch *b, int height, int width, const float *x0, int ld,
+                            int *slot);
+smre_status batch_retrieve_ld(smre_batch *b, int slot, float *x, int ld, smre_result *res);
+
 bool persist_supported(int max_side);
 // shared-memory row stride (power of two >= pitch, 128..1024) or 0 if too wide
 int persist_smem_pitch(int pitch);

@@ -228,3 +228,35 @@ def test_batch_argument_errors(smre, torch_cuda):
         assert B.poll() == [s]
         r = B.retrieve(s)
         assert r.cycles == 3
+
+
+def test_handle_runs_16bit_and_wide_images_through_a_batch(smre, torch_cuda, oracle_mod):
+    """smre_dykstra_* with 16-bit increments, or FP32 wider than the persistent
+    kernel takes, projects through a one-image batch: the same answers."""
+    torch = torch_cuda
+    sides = [1, 2, 3, 4]
+    cS = oracle_mod.bounds(sides, 0.9)
+    (x0,) = images([(40, 1500)], seed0=401)
+    ref = oracle_mod.dykstra(x0.astype(np.float64), sides, cS, max_cycles=6, tol=-1,
+                             n_threads=NTH).x
+    kw = dict(cmode=smre.SMRE_C_EXPLICIT, c_explicit=list(cS), max_cycles=6, tol=-1.0)
+    xd = torch.from_numpy(x0).cuda()
+    group = single(smre, torch, x0, sides, cS, 6, smre.SMRE_F_GROUP_LAUNCHES)
+    with smre.Projector(40, 1500, sides, **kw) as P:        # FP32, 1500 > 1024 columns
+        out = torch.empty_like(xd)
+        r = P.project(xd, out)
+        assert r.cycles == 6 and P.kernel_launches() > 0
+        assert len(P.history()) == 6
+        assert np.array_equal(out.cpu().numpy(), group)
+        P.set_stopping(9, -1.0)                             # more cycles than at creation
+        r = P.project(xd, out)
+        assert r.cycles == 9 and len(P.history()) == 9
+    for qdt in (smre.SMRE_Q_BF16, smre.SMRE_Q_FP16):
+        with smre.Projector(40, 1500, sides, q_dtype=qdt, **kw) as P:
+            out = torch.empty_like(xd)
+            r = P.project(xd, out)
+            assert r.cycles == 6
+            assert err(out.cpu().numpy(), ref) <= 2 * U16[qdt]
+            assert P.device_bytes() > 0
+    with pytest.raises(smre.SmreError):
+        smre.Projector(40, 2100, sides, q_dtype=smre.SMRE_Q_BF16, **kw)   # wider than 2048
