@@ -301,6 +301,61 @@ SMRE_API const char *smre_batch_last_error(const smre_batch *b);
 /* Wait for the stream and free everything (NULL is allowed). */
 SMRE_API void smre_batch_destroy(smre_batch *b);
 
+/* ------------------------------------------------------------------------
+ * Serving: a continuous-batching request loop over a batch.
+ *
+ * Requests (one image each, any size the batch takes) are submitted from any
+ * thread and complete asynchronously.  A loop thread owns the batch: each
+ * round it admits waiting requests in arrival order while a slot and enough
+ * arena bytes are free (admission by increment-storage footprint), runs
+ * cycles_per_round cycles for every admitted image (new requests join between
+ * cycles, their work shares the launches of the others), and retires the
+ * images that stopped, copying each result to the caller's buffer.  A result
+ * does not depend on what else was served with it.
+ * ---------------------------------------------------------------------- */
+typedef struct smre_server smre_server;
+
+typedef struct {
+    smre_batch_params batch;    /* the batch the loop serves from (slots, arena,
+                                   sides, bounds, stopping rule, q_dtype)         */
+    int cycles_per_round;       /* cycles between admission / retirement, >= 1    */
+} smre_server_params;
+
+typedef struct {
+    long long submitted, completed;
+    int waiting;                /* submitted, not yet admitted                    */
+    int active;                 /* admitted, on the GPU                           */
+    int peak_active;
+    long long rounds;
+    double p50_s, p99_s, max_s, mean_s;   /* latency submit -> result, completed */
+    double images_per_s;        /* completed / (last completion - first submit)   */
+} smre_server_counters;
+
+/* Create the batch and start the loop thread (on the calling thread's device). */
+SMRE_API smre_status smre_server_create(const smre_server_params *p, void *cuda_stream,
+                                        smre_server **out);
+
+/* Queue one request: x0 (height x width floats, host or device) is copied
+ * before the call returns; the result goes to x (height x width floats, host
+ * or device) before the request completes.  *ticket identifies it.  EINVAL
+ * when the size is unsupported or needs more than the whole arena. */
+SMRE_API smre_status smre_server_submit(smre_server *s, int height, int width, const float *x0,
+                                        float *x, long long *ticket);
+
+/* Wait up to timeout_s seconds (< 0: no limit) for a request; on completion
+ * fill *res (seconds = latency from submission) and return its status (OK or
+ * ENOTCONVERGED; the ticket is then released).  ETIMEOUT: not finished yet,
+ * the ticket stays valid. */
+SMRE_API smre_status smre_server_wait(smre_server *s, long long ticket, double timeout_s,
+                                      smre_result *res);
+
+/* Counters and latency quantiles so far; returns the status of the last failed
+ * round (OK if none). */
+SMRE_API smre_status smre_server_stats(smre_server *s, smre_server_counters *st);
+
+/* Finish every submitted request, stop the loop, free everything. */
+SMRE_API void smre_server_destroy(smre_server *s);
+
 /* Bytes of device memory the handle holds. */
 SMRE_API size_t smre_dykstra_device_bytes(const smre_dykstra *h);
 

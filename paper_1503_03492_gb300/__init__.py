@@ -30,7 +30,9 @@ __all__ = [
     "smre_batch_image_bytes", "smre_batch_create", "smre_batch_submit", "smre_batch_run",
     "smre_batch_poll", "smre_batch_retrieve", "smre_batch_project", "smre_batch_active",
     "smre_batch_kernel_launches", "smre_batch_device_bytes", "smre_batch_last_error",
-    "smre_batch_destroy", "Batch",
+    "smre_batch_destroy", "Batch", "smre_server_params", "smre_server_counters",
+    "smre_server_create", "smre_server_submit", "smre_server_wait", "smre_server_stats",
+    "smre_server_destroy", "Server",
 ]
 
 SMRE_OK, SMRE_EINVAL, SMRE_ENOMEM, SMRE_ECUDA, SMRE_ETIMEOUT, SMRE_ENOTCONVERGED = range(6)
@@ -52,6 +54,8 @@ EXPORTED = (
     "smre_batch_submit", "smre_batch_run", "smre_batch_poll", "smre_batch_retrieve",
     "smre_batch_project", "smre_batch_active", "smre_batch_kernel_launches",
     "smre_batch_device_bytes", "smre_batch_last_error", "smre_batch_destroy",
+    "smre_server_create", "smre_server_submit", "smre_server_wait", "smre_server_stats",
+    "smre_server_destroy",
 )
 
 
@@ -83,6 +87,23 @@ class smre_batch_params(ctypes.Structure):
         ("q_dtype", ctypes.c_int), ("max_images", ctypes.c_int),
         ("device_bytes", ctypes.c_size_t), ("flags", ctypes.c_int),
     ]
+
+
+class smre_server_params(ctypes.Structure):
+    _fields_ = [("batch", smre_batch_params), ("cycles_per_round", ctypes.c_int)]
+
+
+class smre_server_counters(ctypes.Structure):
+    _fields_ = [
+        ("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong),
+        ("waiting", ctypes.c_int), ("active", ctypes.c_int), ("peak_active", ctypes.c_int),
+        ("rounds", ctypes.c_longlong),
+        ("p50_s", ctypes.c_double), ("p99_s", ctypes.c_double), ("max_s", ctypes.c_double),
+        ("mean_s", ctypes.c_double), ("images_per_s", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class smre_result(ctypes.Structure):
@@ -149,6 +170,12 @@ def load():
         "smre_batch_device_bytes": (ctypes.c_size_t, [H]),
         "smre_batch_last_error": (ctypes.c_char_p, [H]),
         "smre_batch_destroy": (None, [H]),
+        "smre_server_create": (st, [P(smre_server_params), ctypes.c_void_p, P(H)]),
+        "smre_server_submit": (st, [H, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                    ctypes.c_void_p, P(ctypes.c_longlong)]),
+        "smre_server_wait": (st, [H, ctypes.c_longlong, ctypes.c_double, P(smre_result)]),
+        "smre_server_stats": (st, [H, P(smre_server_counters)]),
+        "smre_server_destroy": (None, [H]),
         "smre_last_error": (ctypes.c_char_p, [H]),
         "smre_version": (ctypes.c_char_p, []),
     }
@@ -507,6 +534,92 @@ class Batch:
         if self.b:
             smre_batch_destroy(self.b)
             self.b = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ serving
+
+def smre_server_create(batch_params: smre_batch_params, cycles_per_round=4, stream=None):
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    p = smre_server_params()
+    p.batch = batch_params
+    p.cycles_per_round = int(cycles_per_round)
+    s = ctypes.c_void_p()
+    _check(load().smre_server_create(ctypes.byref(p), ctypes.c_void_p(stream or 0),
+                                     ctypes.byref(s)))
+    return s.value
+
+
+def smre_server_submit(s, x0, x) -> int:
+    """Queue x0 (H x W); the result lands in x (same shape).  Returns the ticket."""
+    p0, k0 = _ptr(x0)
+    p1, k1 = _ptr(x)
+    H, W = x0.shape
+    t = ctypes.c_longlong()
+    _check(load().smre_server_submit(s, int(H), int(W), p0, p1, ctypes.byref(t)))
+    return t.value
+
+
+def smre_server_wait(s, ticket, timeout_s=-1.0):
+    """Result of a request (None if it did not finish within timeout_s)."""
+    res = smre_result()
+    st = load().smre_server_wait(s, int(ticket), float(timeout_s), ctypes.byref(res))
+    if st == SMRE_ETIMEOUT:
+        return None
+    _check(st, None, ok=(SMRE_OK, SMRE_ENOTCONVERGED))
+    return res
+
+
+def smre_server_stats(s):
+    c = smre_server_counters()
+    load().smre_server_stats(s, ctypes.byref(c))
+    return c
+
+
+def smre_server_destroy(s):
+    load().smre_server_destroy(s)
+
+
+class Server:
+    """Continuous-batching request loop: ``with Server(sides, ...) as S: t = S.submit(x0, x); S.wait(t)``.
+    The output arrays passed to ``submit`` are kept alive until their request is waited for."""
+
+    def __init__(self, sides, cycles_per_round=4, stream=None, **batch_kw):
+        self.params = make_batch_params(sides, **batch_kw)
+        self.s = smre_server_create(self.params, cycles_per_round, stream)
+        self._keep = {}
+
+    def submit(self, x0, x):
+        t = smre_server_submit(self.s, x0, x)
+        self._keep[t] = x
+        return t
+
+    def wait(self, ticket, timeout_s=-1.0):
+        r = smre_server_wait(self.s, ticket, timeout_s)
+        if r is not None:
+            self._keep.pop(ticket, None)
+        return r
+
+    def stats(self):
+        return smre_server_stats(self.s)
+
+    def close(self):
+        if self.s:
+            smre_server_destroy(self.s)
+            self.s = None
+            self._keep.clear()
 
     def __enter__(self):
         return self

@@ -664,6 +664,18 @@ void smre_batch_destroy(smre_batch *b) { free_batch(b); }
 
 namespace smre {
 
+void batch_drop(smre_batch *b, int slot)
+{
+    if (!b || slot < 0 || slot >= b->max_images || !b->slots[slot].used) return;
+    auto &sl = b->slots[slot];
+    cudaStreamSynchronize(b->stream);
+    b->heap.release(sl.off, sl.bytes);
+    sl.used = false;
+    sl.done = false;
+    b->active.erase(std::find(b->active.begin(), b->active.end(), slot));
+    b->dirty = true;
+}
+
 smre_status batch_set_rule(smre_batch *b, int max_cycles, double tol, int tol_relative)
 {
     if (max_cycles > b->hist_cap)

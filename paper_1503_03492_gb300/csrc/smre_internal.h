@@ -195,6 +195,8 @@ cudaError_t launch_batch_decide(const BDecideArgs &A, cudaStream_t s);
 // change the stopping rule (max_cycles up to the history the batch was made
 // for), or project one device image and copy its history and control block.
 smre_status batch_set_rule(smre_batch *b, int max_cycles, double tol, int tol_relative);
+// free a slot whatever its state (after a failed round)
+void batch_drop(smre_batch *b, int slot);
 smre_status batch_run_one(smre_batch *b, int height, int width, const float *x0, float *x,
                           int ld, double *hist, int hist_cap, Control *ctl_out);
 // submit / retrieve with a row stride of ld floats for the caller's image
