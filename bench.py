@@ -14,6 +14,13 @@ flushed between timed steps.
 
 --impl reference times the FP64 CPU oracle on this host's cores on a bounded
 sample of the same workload (the reference arm of this benchmark).
+
+On one GPU the line also carries "extras" (skip with --no-extras): the uneven
+batch of 256 images (BF16 and FP32 increments against one projection per
+image), mixed-precision increments on a 2048 x 2048 image (throughput and
+error against the FP64 oracle), and the continuous-batching request loop on a
+Poisson request stream (p50 / p99 latency and images/s against the plain
+single-image API).
 Multi-GPU: independent replicas (one image per rank, no collective on the
 data path); weak scaling.
 """
@@ -195,6 +202,191 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------------------ extras
+# The other workloads of the method, reported beside the main line (rank 0 of
+# a one-GPU run): the uneven batch, mixed-precision increments on a large
+# image, and the continuous-batching request loop.
+
+def q_bytes_per_cycle(shapes, sides, qdt):
+    """Algorithmic bytes of one cycle: every window's increments read and
+    written (FP32: 8 L^2 bytes; 16-bit: 4 L^2 + 8 with the window scale), plus
+    the x_prev read and write of the norm (8 bytes a pixel)."""
+    tot = 0
+    for (h, w) in shapes:
+        for L in sides:
+            nw = (h - L + 1) * (w - L + 1)
+            tot += nw * (8 * L * L if qdt == 0 else 4 * L * L + 8)
+        tot += 8 * h * w
+    return tot
+
+
+def windows_per_cycle(shapes, sides):
+    return sum((h - L + 1) * (w - L + 1) for (h, w) in shapes for L in sides)
+
+
+def timed_batch_cycles(smre, torch, xs, sides, cS, qdt, cycles, stream):
+    """Per-cycle device time of a batch over xs (device tensors): the first
+    cycle (no increments to read) runs untimed, then `cycles` timed."""
+    need = sum(smre.smre_batch_image_bytes(smre.make_batch_params(sides, q_dtype=qdt,
+                                                                  max_cycles=cycles + 1), *x.shape)
+               for x in xs)
+    with smre.Batch(sides, stream=stream, cmode=smre.SMRE_C_EXPLICIT, c_explicit=cS, q_dtype=qdt,
+                    max_cycles=cycles + 1, tol=-1.0, max_images=len(xs),
+                    device_bytes=need + (64 << 20)) as B:
+        for x in xs:
+            assert B.submit(x) >= 0
+        B.run(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        B.run(cycles)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        done = B.poll()
+        outs = {}
+        for s in done:
+            outs[s] = B.retrieve(s)
+        launches = B.kernel_launches()
+    return e0.elapsed_time(e1) / 1e3 / cycles, launches
+
+
+def bench_batched(smre, torch, stream, peak):
+    """256 residual images, sides s in {128..1024}, half of them s x 2s, window
+    sides 1..8: batched launches (BF16 and FP32 increments) against one
+    projection per image through the single-image API (FP32)."""
+    from synthetic import batch_images
+    xs_h = [np.ascontiguousarray(a, np.float32) for a in batch_images(256)]
+    xs = [torch.from_numpy(a).cuda() for a in xs_h]
+    shapes = [x.shape for x in xs_h]
+    cS = smre.smre_bounds(smre.make_params(64, 64, SIDES, alpha=ALPHA))
+    wpc = windows_per_cycle(shapes, SIDES)
+    out = {"images": len(xs), "pixels": int(sum(h * w for h, w in shapes)), "sides": "1..8",
+           "windows_per_cycle": wpc}
+    cycles = 4
+    for name, qdt in (("bf16", smre.SMRE_Q_BF16), ("fp32", smre.SMRE_Q_FP32)):
+        sec, _ = timed_batch_cycles(smre, torch, xs, SIDES, cS, qdt, cycles, stream)
+        gbs = q_bytes_per_cycle(shapes, SIDES, qdt) / sec / 1e9
+        out[name] = {"ms_per_cycle": 1e3 * sec, "window_projections_per_s": wpc / sec,
+                     "achieved_gbs": gbs, "frac_of_measured_hbm": gbs / peak}
+    # one launch per image (FP32 single-image API), on the first 24 images
+    tot_w, tot_s = 0, 0.0
+    for x in xs[:24]:
+        h, w = x.shape
+        with smre.Projector(h, w, SIDES, stream=stream, cmode=smre.SMRE_C_EXPLICIT, c_explicit=cS,
+                            max_cycles=3, tol=-1.0) as P:
+            o = torch.empty_like(x)
+            P.project(x, o)                       # first cycles and allocation untimed
+            r = P.project(x, o)
+            tot_w += r.windows
+            tot_s += r.seconds
+    out["one_launch_per_image_fp32"] = {"window_projections_per_s": tot_w / tot_s,
+                                        "sample": "first 24 images, 3 cycles each"}
+    out["speedup_bf16_vs_one_launch_per_image"] = (out["bf16"]["window_projections_per_s"] /
+                                                   (tot_w / tot_s))
+    return out
+
+
+def bench_mixed(smre, torch, stream, peak, threads):
+    """One 2048 x 2048 residual (1600 emitters), window sides 1..12: FP32 vs
+    BF16 vs FP16 increments with per-window scales; error against the FP64
+    oracle measured on a 256 x 256 crop with the same sides."""
+    import oracle
+    from synthetic import emitter_residual_2048
+    sides = list(range(1, 13))
+    x_h = np.ascontiguousarray(emitter_residual_2048(), np.float32)
+    x = torch.from_numpy(x_h).cuda()
+    cS = smre.smre_bounds(smre.make_params(64, 64, sides, alpha=ALPHA))
+    shapes = [x_h.shape]
+    wpc = windows_per_cycle(shapes, sides)
+    out = {"image": "2048x2048", "sides": "1..12", "windows_per_cycle": wpc}
+    cycles = 3
+    res = {}
+    for name, qdt in (("fp32", 0), ("bf16", 1), ("fp16", 2)):
+        sec, _ = timed_batch_cycles(smre, torch, [x], sides, cS, qdt, cycles, stream)
+        gbs = q_bytes_per_cycle(shapes, sides, qdt) / sec / 1e9
+        out[name] = {"ms_per_cycle": 1e3 * sec, "window_projections_per_s": wpc / sec,
+                     "achieved_gbs": gbs, "frac_of_measured_hbm": gbs / peak}
+    # accuracy: 10 cycles on a crop, each storage type against the FP64 oracle
+    crop = np.ascontiguousarray(x_h[:256, :256])
+    ref = oracle.dykstra(crop.astype(np.float64), sides, cS, max_cycles=10, tol=-1,
+                         n_threads=threads).x
+    scale = np.abs(ref).max()
+    for name, qdt in (("fp32", 0), ("bf16", 1), ("fp16", 2)):
+        with smre.Projector(256, 256, sides, stream=stream, cmode=smre.SMRE_C_EXPLICIT,
+                            c_explicit=cS, max_cycles=10, tol=-1.0, q_dtype=qdt) as P:
+            o = np.empty_like(crop)
+            P.project(crop, o)
+        res[name] = float(np.abs(o.astype(np.float64) - ref).max() / scale)
+        out[name]["err_vs_fp64_oracle"] = res[name]
+    out["accuracy_sample"] = "256x256 crop, sides 1..12, 10 cycles, max-abs relative"
+    return out
+
+
+def bench_serving(smre, torch, stream, n_req=64, rate=500.0):
+    """Poisson arrivals (mean `rate` per second) of square SOFI-like requests,
+    side uniform in 64..2048, window sides 1..8, BF16 increments, at most 100
+    cycles or a relative step of 1e-6: the request loop against the plain
+    single-image API (FP32, one request at a time, in arrival order)."""
+    from synthetic import request_stream, request_image, sofi_canvas
+    canvas = sofi_canvas()
+    reqs = request_stream(n=n_req, rate=rate)
+    imgs = [np.ascontiguousarray(request_image(canvas, side, sd), np.float32)
+            for (_, side, sd) in reqs]
+    arrivals = [a for (a, _, _) in reqs]
+    cS = smre.smre_bounds(smre.make_params(64, 64, SIDES, alpha=ALPHA))
+    kw = dict(cmode=smre.SMRE_C_EXPLICIT, c_explicit=cS, max_cycles=100, tol=1e-6,
+              tol_relative=True)
+    outs = [np.empty_like(a) for a in imgs]
+    with smre.Server(SIDES, cycles_per_round=4, stream=stream, q_dtype=smre.SMRE_Q_BF16,
+                     max_images=64, device_bytes=48 << 30, **kw) as S:
+        t0 = time.perf_counter()
+        tickets = []
+        for a, img, o in zip(arrivals, imgs, outs):
+            d = t0 + a - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            tickets.append(S.submit(img, o))
+        for t in tickets:
+            S.wait(t)
+        st = S.stats()
+    served = {"images_per_s": st.images_per_s, "p50_s": st.p50_s, "p99_s": st.p99_s,
+              "max_s": st.max_s, "peak_active": st.peak_active, "rounds": st.rounds}
+    # the plain path on the same stream: one request at a time, arrival order
+    lat = []
+    t0 = time.perf_counter()
+    for a, img in zip(arrivals, imgs):
+        d = t0 + a - time.perf_counter()
+        if d > 0:
+            time.sleep(d)
+        h, w = img.shape
+        with smre.Projector(h, w, SIDES, stream=stream, **kw) as P:
+            o = np.empty_like(img)
+            P.project(img, o)
+        lat.append(time.perf_counter() - t0 - a)
+    t_plain = time.perf_counter() - t0
+    lat.sort()
+    plain = {"images_per_s": n_req / t_plain, "p50_s": lat[len(lat) // 2],
+             "p99_s": lat[min(len(lat) - 1, int(round(0.99 * (len(lat) - 1))))]}
+    return {"requests": n_req, "rate_per_s": rate, "sides": "1..8",
+            "stop": "rel step < 1e-6 or 100 cycles", "served_bf16": served,
+            "plain_single_image_fp32": plain,
+            "images_per_s_ratio": served["images_per_s"] / plain["images_per_s"]}
+
+
+def run_extras(smre, torch, stream, peak, threads):
+    out = {}
+    for name, fn in (("batched_256_uneven", lambda: bench_batched(smre, torch, stream, peak)),
+                     ("mixed_precision_2048", lambda: bench_mixed(smre, torch, stream, peak, threads)),
+                     ("serving_poisson", lambda: bench_serving(smre, torch, stream))):
+        t = time.perf_counter()
+        try:
+            out[name] = fn()
+        except Exception as e:   # a failed extra is reported, the main line stands
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+        out[name]["wall_s"] = time.perf_counter() - t
+        torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -202,6 +394,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched, mixed-precision and serving workloads")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -302,6 +496,11 @@ def main():
                          f"incomplete projection of the same image, FP64 C oracle, "
                          f"{threads} OpenMP threads ({sv:.1f} s)"}
 
+    extras = None
+    if rank == 0 and world == 1 and not args.no_extras:
+        P.close()
+        extras = run_extras(smre, torch, stream, peak, os.cpu_count() or 1)
+
     if rank == 0:
         line = {
             "metric": "window-projections/s", "value": value, "unit": "window-projections/s",
@@ -326,6 +525,7 @@ def main():
                     "h2d_bytes_per_step": 2 * H * W * 4, "d2h_bytes_per_step": 2 * H * W * 4},
             "gpu_launches": launches,
             "clocks": clocks,
+            "extras": extras,
         }
         print(json.dumps(line), flush=True)
     P.close()

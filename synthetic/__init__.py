@@ -113,6 +113,77 @@ def sofi_like(side=256, frames=200, density=20, on_prob=0.3, psf_sigma=1.5, peak
     return r / r.std()
 
 
+def sofi_tile(side=512, frames=200, density=20, on_prob=0.3, psf_sigma=1.5, peak=100.0,
+              background=10.0, seed=1005):
+    """The same second-order-cumulant-like residual as ``sofi_like`` for larger
+    sides: every emitter's PSF (exact within 6 sigma) is a column of a sparse
+    pixel x emitter matrix, so a frame is one sparse product."""
+    import scipy.sparse as sp
+    rng = np.random.default_rng(seed)
+    ne = max(1, int(round(density * side * side / (64 * 64))))
+    cy = rng.uniform(0, side, size=ne)
+    cx = rng.uniform(0, side, size=ne)
+    rad = int(np.ceil(6 * psf_sigma))
+    d = np.arange(-rad, rad + 2)
+    rows, cols, vals = [], [], []
+    for k in range(ne):
+        yy = int(cy[k]) + d
+        xx = int(cx[k]) + d
+        yy = yy[(yy >= 0) & (yy < side)]
+        xx = xx[(xx >= 0) & (xx < side)]
+        g = peak * np.exp(-((yy[:, None] - cy[k]) ** 2 + (xx[None, :] - cx[k]) ** 2)
+                          / (2.0 * psf_sigma * psf_sigma))
+        idx = (yy[:, None] * side + xx[None, :]).ravel()
+        rows.append(idx)
+        cols.append(np.full(idx.size, k))
+        vals.append(g.ravel())
+    M = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                      shape=(side * side, ne))
+    s1 = np.zeros(side * side)
+    s2 = np.zeros(side * side)
+    for _ in range(frames):
+        on = (rng.random(ne) < on_prob).astype(np.float64)
+        y = rng.poisson(background + M @ on).astype(np.float64)
+        s1 += y
+        s2 += y * y
+    var = (s2 / frames - (s1 / frames) ** 2).reshape(side, side)
+    r = var - _smooth(var, 4.0)
+    return r / r.std()
+
+
+def sofi_canvas(side=2048, tile=512, n_tiles=2, seed=1005):
+    """A ``side`` x ``side`` SOFI-like residual assembled from ``n_tiles``
+    independently drawn ``sofi_tile`` tiles, each placement flipped and
+    transposed at random (the statistics are local, so the mosaic keeps them);
+    requests of the serving workload are crops of it."""
+    rng = np.random.default_rng(seed)
+    tiles = [sofi_tile(tile, seed=seed + 17 * k) for k in range(n_tiles)]
+    out = np.empty((side, side))
+    for ty in range(0, side, tile):
+        for tx in range(0, side, tile):
+            t = tiles[rng.integers(n_tiles)]
+            if rng.random() < 0.5:
+                t = t.T
+            if rng.random() < 0.5:
+                t = t[::-1]
+            if rng.random() < 0.5:
+                t = t[:, ::-1]
+            h, w = min(tile, side - ty), min(tile, side - tx)
+            out[ty:ty + h, tx:tx + w] = t[:h, :w]
+    return out
+
+
+def request_image(canvas, side, seed):
+    """A ``side`` x ``side`` request cropped from ``canvas`` at a seeded offset,
+    normalised by its own standard deviation."""
+    rng = np.random.default_rng(seed)
+    H, W = canvas.shape
+    y0 = int(rng.integers(0, H - side + 1))
+    x0 = int(rng.integers(0, W - side + 1))
+    c = canvas[y0:y0 + side, x0:x0 + side]
+    return c / c.std()
+
+
 def request_stream(n=2000, rate=500.0, seed=1006):
     """Poisson arrivals (mean ``rate`` per second) of square requests with side
     uniform in 64..2048: list of (arrival_time_s, side, seed)."""
