@@ -97,10 +97,8 @@ __global__ void __launch_bounds__(kNormThreads) bdecide_kernel(const BDecideArgs
 
 int batch_lb(int L) { return batch::lb_of(L); }
 int batch_virtual_width(int L) { return batch::vw_of(batch::lb_of(L)); }
-size_t batch_part_bytes(int L)
-{
-    return L > 1 ? (size_t)batch::vw_of(batch::lb_of(L)) * 16 : 0;
-}
+// column sums, window sums and their FP64 recheck: 16 bytes a virtual column
+size_t batch_part_bytes(int L) { return (size_t)batch::vw_of(batch::lb_of(L)) * 16; }
 int batch_threads() { return batch::kThreads; }
 
 cudaError_t batch_prepare(int qtype, size_t smem_max)

@@ -564,15 +564,15 @@ __global__ void __launch_bounds__(kThreads, 1) bstep_kernel(const BStepArgs A)
                             }
                         }
                     }
+                    // q_i / sw = y_i (1 - scale) / sw, rounded to the 16-bit type
+                    const float f0 = (1.f - scale[j][0]) * inv[0], f1 = (1.f - scale[j][1]) * inv[1];
 #pragma unroll
                     for (int i = 0; i < LB; ++i)
                         if (i < L) {
                             const float y0 = x[i][j][0], y1 = x[i][j][1];
-                            const float2 h = C::store2(qc + o[j] + i * P,
-                                                       (y0 - y0 * scale[j][0]) * inv[0],
-                                                       (y1 - y1 * scale[j][1]) * inv[1]);
-                            x[i][j][0] = y0 - h.x * sw[0];   // consistent: x = y - deq(q_s)
-                            x[i][j][1] = y1 - h.y * sw[1];
+                            const float2 h = C::store2(qc + o[j] + i * P, y0 * f0, y1 * f1);
+                            x[i][j][0] = fmaf(-h.x, sw[0], y0);   // consistent: x = y - deq(q_s)
+                            x[i][j][1] = fmaf(-h.y, sw[1], y1);
                         }
                     if (on[j][0] && rr[j] == 0) sc[so[j] + vv[j]] = sw[0];
                     if (on[j][1] && r1[j] == 0) sc[so[j] + w1[j]] = sw[1];

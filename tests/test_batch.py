@@ -17,6 +17,16 @@ pytestmark = pytest.mark.gpu
 
 TOL = 1e-5
 NTH = os.cpu_count() or 1
+# unit roundoff of the stored increments: BF16 keeps 8 significant bits, FP16 11
+U16 = {1: 2.0 ** -8, 2: 2.0 ** -11}
+# Each set update with 16-bit increments is the exact projection plus a
+# perturbation of at most u |q_i| per pixel (x = y - deq(q), deq(q) = q (1 + d),
+# |d| <= u), and |q_i| <= |y_i|.  The perturbations of successive sets and
+# cycles partly cancel; no bound on their sum is proven here.  Measured on
+# these inputs: 1.0 u to 2.4 u of max |x| after 3 to 20 cycles.  The tests
+# hold the error to this envelope (and report it): a broken path lands far
+# outside (NaN, or errors of the order of the increments themselves).
+U16_ENVELOPE = 4.0
 
 
 @pytest.fixture(scope="module")
@@ -88,6 +98,29 @@ def test_fp32_batch_equals_single_path_and_oracle(smre, torch_cuda, oracle_mod, 
             assert np.array_equal(one, out), (x0.shape, flags, np.abs(one - out).max())
 
 
+def test_many_items_per_cta(smre, torch_cuda, oracle_mod):
+    """A tall, wide image gives every CTA many items, so the shared-memory ring
+    wraps many times in one launch (window sides 1..3, all increment types)."""
+    sides = [1, 2, 3]
+    cS = oracle_mod.bounds(sides, 0.9)
+    (x0,) = images([(1500, 2048)], seed0=601)
+    kw = dict(cmode=smre.SMRE_C_EXPLICIT, c_explicit=list(cS), max_cycles=3, tol=-1.0,
+              max_images=1, device_bytes=2 << 30)
+    ref = oracle_mod.dykstra(x0.astype(np.float64), sides, cS, max_cycles=3, tol=-1,
+                             n_threads=NTH).x
+    group = single(smre, torch_cuda, x0, sides, cS, 3, smre.SMRE_F_GROUP_LAUNCHES)
+    for qdt in (smre.SMRE_Q_FP32, smre.SMRE_Q_BF16, smre.SMRE_Q_FP16):
+        out = np.full_like(x0, np.nan)
+        with smre.Batch(sides, q_dtype=qdt, **kw) as B:
+            B.project([x0], [out])
+        assert np.isfinite(out).all(), qdt
+        if qdt == smre.SMRE_Q_FP32:
+            assert np.array_equal(out, group)
+            assert err(out, ref) <= TOL
+        else:
+            assert err(out, ref) <= U16_ENVELOPE * U16[qdt], (qdt, err(out, ref))
+
+
 def test_device_images_and_per_image_stopping(smre, torch_cuda, oracle_mod):
     """Images stop at their own cycle (relative step test); each matches the
     oracle run for the same number of cycles."""
@@ -147,17 +180,12 @@ def test_result_is_the_same_alone_and_in_the_mix(smre, torch_cuda, oracle_mod):
     assert err(alone, ref) <= TOL
 
 
-# unit roundoff of the stored increments: BF16 keeps 8 significant bits, FP16 11
-U16 = {1: 2.0 ** -8, 2: 2.0 ** -11}
-
-
 @pytest.mark.parametrize("qdt", [1, 2])
 def test_mixed_precision_error_against_oracle(smre, torch_cuda, oracle_mod, qdt):
-    """16-bit increments: each stored increment carries a relative rounding
-    error of at most the type's unit roundoff u, and |q_s| <= |x0 - x|, so the
-    error against the FP64 oracle stays within 2 u of max |x| (max-abs
-    relative); the FP32 path of the same batch stays within 1e-5."""
-    bound = 2 * U16[qdt]
+    """16-bit increments: error against the FP64 oracle within the envelope of
+    the type's unit roundoff (max-abs relative); the FP32 path of the same
+    batch stays within 1e-5."""
+    bound = U16_ENVELOPE * U16[qdt]
     sides = list(range(1, 9))
     cS = oracle_mod.bounds(sides, 0.9)
     (x0, y0) = images([(96, 128), (64, 200)], seed0=307)
@@ -256,7 +284,7 @@ def test_handle_runs_16bit_and_wide_images_through_a_batch(smre, torch_cuda, ora
             out = torch.empty_like(xd)
             r = P.project(xd, out)
             assert r.cycles == 6
-            assert err(out.cpu().numpy(), ref) <= 2 * U16[qdt]
+            assert err(out.cpu().numpy(), ref) <= U16_ENVELOPE * U16[qdt]
             assert P.device_bytes() > 0
     with pytest.raises(smre.SmreError):
         smre.Projector(40, 2100, sides, q_dtype=smre.SMRE_Q_BF16, **kw)   # wider than 2048
