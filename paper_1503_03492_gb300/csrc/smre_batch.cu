@@ -97,8 +97,12 @@ __global__ void __launch_bounds__(kNormThreads) bdecide_kernel(const BDecideArgs
 
 int batch_lb(int L) { return batch::lb_of(L); }
 int batch_virtual_width(int L) { return batch::vw_of(batch::lb_of(L)); }
-// column sums, window sums and their FP64 recheck: 16 bytes a virtual column
-size_t batch_part_bytes(int L) { return (size_t)batch::vw_of(batch::lb_of(L)) * 16; }
+// column sums, the FP64 recheck and the window factors: 16 bytes a virtual
+// column with FP32 increments, 20 with 16-bit ones
+size_t batch_part_bytes(int L, int qtype)
+{
+    return (size_t)batch::vw_of(batch::lb_of(L)) * (qtype == 0 ? 16 : 20);
+}
 int batch_threads() { return batch::kThreads; }
 
 cudaError_t batch_prepare(int qtype, size_t smem_max)

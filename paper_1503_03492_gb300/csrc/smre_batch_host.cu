@@ -375,7 +375,7 @@ smre_status smre_batch_create(const smre_batch_params *p, void *cuda_stream, smr
     b->smem = (size_t)optin - 1024;   // leave room for the kernel's static shared memory
     // the ring must hold the largest block of any step
     for (int L : sides) {
-        const size_t ring = b->smem - 256 - batch_part_bytes(L);
+        const size_t ring = b->smem - 256 - batch_part_bytes(L, b->qtype);
         const size_t need = (size_t)L * batch_virtual_width(L) * 4;
         if (need > ring) {
             bfail(b, SMRE_EINVAL, "side %d: block of %zu bytes above the %zu-byte ring", L, need, ring);
@@ -509,7 +509,7 @@ smre_status smre_batch_run(smre_batch *b, int cycles)
             A.cS = (float)b->cS_of[st.L];
             A.sqrt_cS = (float)std::sqrt(b->cS_of[st.L]);
             A.cS64 = b->cS_of[st.L];
-            A.ring_offset = (int)(256 + batch_part_bytes(st.L));
+            A.ring_offset = (int)(256 + batch_part_bytes(st.L, b->qtype));
             A.ring_bytes = (int)(b->smem - A.ring_offset);
             A.timeout_ns = b->timeout_ns;
             A.err = b->d_err;

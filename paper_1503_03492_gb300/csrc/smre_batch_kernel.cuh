@@ -104,7 +104,7 @@ struct QConv<__half> {
 // unroll with fixed offsets) and once for sides 13..16 (run-time L <= 16).
 __host__ __device__ constexpr int lb_of(int L) { return L <= 12 ? L : 16; }
 // column pairs per consumer thread: x of an item takes 2 LB CPP registers
-__host__ __device__ constexpr int cpp_of(int LB) { return LB == 1 ? 4 : LB == 2 ? 3 : 2; }
+__host__ __device__ constexpr int cpp_of(int LB) { return LB == 2 ? 3 : 2; }
 constexpr int kOutside = -(1 << 24);   // window index of a column outside the item
 __host__ __device__ constexpr int vw_of(int LB) { return 2 * kNC * cpp_of(LB); }
 __host__ __device__ constexpr int round16(int v) { return (v + 15) & ~15; }
@@ -127,6 +127,59 @@ __device__ __forceinline__ float pow2_above(float v, int shift, int &ex)
     const int r = ex + shift + 127;
     if (!(v > 0.f) || be == 0 || be == 255 || r < 1 || r > 254) return 0.f;
     return __uint_as_float((unsigned)r << 23);
+}
+
+// What the columns of a window need from its leader: the scale of the ball
+// test (FP32 increments), or f = (1 - scale) / sw and the power-of-two sw
+// (16-bit increments: q_i / sw = f y_i, x_i = y_i - sw h_i).
+template <bool MIXED>
+struct WinData;
+template <>
+struct WinData<false> {
+    using type = float;
+    __device__ static float none() { return 1.f; }
+    __device__ static float scale(float d) { return d; }
+    __device__ static float f(float) { return 0.f; }
+    __device__ static float sw(float) { return 0.f; }
+};
+template <>
+struct WinData<true> {
+    using type = float2;
+    __device__ static float2 none() { return make_float2(0.f, 0.f); }
+    __device__ static float scale(float2) { return 1.f; }
+    __device__ static float f(float2 d) { return d.x; }
+    __device__ static float sw(float2 d) { return d.y; }
+};
+
+// Factors of one window from its sum of squares t: x = y * scale with
+// scale = sqrt(cS / t) if t > cS (Eq. dykstra:if); for 16-bit increments sw,
+// a power of two with |q_i| / sw <= 2^15 from |q_i| <= (1 - scale) sqrt(t),
+// and f = (1 - scale) / sw.  With `exact`, the FP64 sum t64 against cS64
+// decides and gives the scale (the recheck of windows near the boundary).
+template <bool MIXED>
+__device__ __forceinline__ typename WinData<MIXED>::type window_factors(float t, float cS,
+                                                                        float sqrt_cS, double t64,
+                                                                        double cS64, bool exact)
+{
+    float scale = 1.f;
+    if (exact) {
+        if (t64 > cS64) scale = (float)sqrt(cS64 / t64);
+    } else if (t > cS) {
+        scale = sqrt_cS * rsqrtf(t);
+    }
+    if constexpr (!MIXED) {
+        return scale;
+    } else {
+        float f = 0.f, sw = 0.f;
+        const float qn = (1.f - scale) * (t * rsqrtf(t));
+        int ex;
+        const float s = pow2_above(qn, -14, ex);
+        if (s > 0.f) {
+            sw = s;
+            f = (1.f - scale) * __uint_as_float((unsigned)(127 + 14 - ex) << 23);
+        }
+        return make_float2(f, sw);
+    }
 }
 
 __device__ __forceinline__ int find_active(const int *prefix, int n_active, int item)
@@ -327,9 +380,13 @@ __global__ void __launch_bounds__(kThreads, 1) bstep_kernel(const BStepArgs A)
     uint64_t *written = full + kD;                          // [kD] chunk free again
     uint64_t *ready = written + kD;                         // [kD] new increments in the chunk
     int *s_off = reinterpret_cast<int *>(ready + kD);       // [kD] ring offset of each chunk
-    float *part = reinterpret_cast<float *>(smem + 256);    // [VW] column sums of y^2
-    float *wsum = part + VW;                                // [VW] window sums, at the first column
-    double *part64 = reinterpret_cast<double *>(wsum + VW); // [VW] FP64 recheck
+    // per virtual column: the column sum of y^2, the FP64 recheck sums and,
+    // at each window's first column, the window's factors (the scale of the
+    // ball test; for 16-bit increments f = (1 - scale) / sw and sw instead)
+    using WD = typename WinData<MIXED>::type;
+    float *part = reinterpret_cast<float *>(smem + 256);            // [VW]
+    double *part64 = reinterpret_cast<double *>(part + VW);         // [VW]
+    WD *wdat = reinterpret_cast<WD *>(part64 + VW);                 // [VW]
     unsigned char *ring = smem + A.ring_offset;
     __shared__ volatile int s_abort;
 
@@ -460,12 +517,18 @@ __global__ void __launch_bounds__(kThreads, 1) bstep_kernel(const BStepArgs A)
             }
 
             // one thread per window (its first column) sums the L column sums in
-            // column order; windows within the band of the ball test are flagged
+            // column order, takes the ball test of Eq. (dykstra:if) and, for
+            // 16-bit increments, picks the window's power-of-two scale sw with
+            // |q_i| / sw <= 2^15 (FP16 holds up to 65504) from
+            // |q_i| <= |q_s|_2 = (1 - scale) sqrt(t); windows within the band
+            // of the test are flagged for the FP64 recheck
             bool near = false;
+            float tl[CPP][2];   // window sums held by their leaders
 #pragma unroll
             for (int j = 0; j < CPP; ++j)
 #pragma unroll
                 for (int e = 0; e < 2; ++e) {
+                    tl[j][e] = 0.f;
                     if (!on[j][e] || (e ? r1[j] : rr[j]) != 0) continue;
                     const float *pp = part + po[j] + e;
                     float pv[LB];
@@ -475,25 +538,11 @@ __global__ void __launch_bounds__(kThreads, 1) bstep_kernel(const BStepArgs A)
 #pragma unroll
                     for (int m = 0; m < LB; ++m)
                         if (m < L) ts += pv[m];
-                    wsum[po[j] + e] = ts;
+                    tl[j][e] = ts;
                     if (fabsf(ts - cS) <= kNearBand * cS) near = true;
+                    wdat[po[j] + e] = window_factors<MIXED>(ts, cS, sqrt_cS, 0.0, 0.0, false);
                 }
-            const bool any_near = named_sync_or(1, near, kNC);
-
-            // the ball test of Eq. (dykstra:if) per owned column
-            float scale[CPP][2], tsv[CPP][2];
-#pragma unroll
-            for (int j = 0; j < CPP; ++j)
-#pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    scale[j][e] = 1.f;
-                    tsv[j][e] = 0.f;
-                    if (!on[j][e]) continue;
-                    const float ts = wsum[po[j] + e - (e ? r1[j] : rr[j])];
-                    tsv[j][e] = ts;
-                    if (ts > cS) scale[j][e] = sqrt_cS * rsqrtf(ts);
-                }
-            if (any_near) {
+            if (named_sync_or(1, near, kNC)) {
                 // rare: windows within the band get their sums again in FP64
 #pragma unroll
                 for (int j = 0; j < CPP; ++j)
@@ -513,22 +562,22 @@ __global__ void __launch_bounds__(kThreads, 1) bstep_kernel(const BStepArgs A)
 #pragma unroll
                     for (int e = 0; e < 2; ++e) {
                         if (!on[j][e] || (e ? r1[j] : rr[j]) != 0) continue;
-                        if (fabsf(tsv[j][e] - cS) > kNearBand * cS) continue;
+                        if (fabsf(tl[j][e] - cS) > kNearBand * cS) continue;
                         double t64 = 0.0;
                         for (int m = 0; m < L; ++m) t64 += part64[po[j] + e + m];
-                        part64[po[j] + e] = t64;   // the window's FP64 sum, at its first column
+                        wdat[po[j] + e] = window_factors<MIXED>((float)t64, cS, sqrt_cS, t64, A.cS64,
+                                                                true);
                     }
                 named_sync(1, kNC);
-#pragma unroll
-                for (int j = 0; j < CPP; ++j)
-#pragma unroll
-                    for (int e = 0; e < 2; ++e) {
-                        if (!on[j][e] || fabsf(tsv[j][e] - cS) > kNearBand * cS) continue;
-                        const double t64 = part64[po[j] + e - (e ? r1[j] : rr[j])];
-                        scale[j][e] = t64 > A.cS64 ? (float)sqrt(A.cS64 / t64) : 1.f;
-                        tsv[j][e] = (float)t64;
-                    }
             }
+            // every owned column takes its window's factors
+            WD wf[CPP][2];
+#pragma unroll
+            for (int j = 0; j < CPP; ++j)
+#pragma unroll
+                for (int e = 0; e < 2; ++e)
+                    wf[j][e] = on[j][e] ? wdat[po[j] + e - (e ? r1[j] : rr[j])]
+                                        : WinData<MIXED>::none();
 
             // x = p_s(y), q_s = y - x; the new increments go into the chunk,
             // which the storer copies to the plane
@@ -536,46 +585,30 @@ __global__ void __launch_bounds__(kThreads, 1) bstep_kernel(const BStepArgs A)
             for (int j = 0; j < CPP; ++j) {
                 if (!(on[j][0] || on[j][1])) continue;
                 if (!MIXED) {
+                    const float c0 = WinData<MIXED>::scale(wf[j][0]), c1 = WinData<MIXED>::scale(wf[j][1]);
 #pragma unroll
                     for (int i = 0; i < LB; ++i)
                         if (i < L) {
                             const float y0 = x[i][j][0], y1 = x[i][j][1];
-                            const float n0 = y0 * scale[j][0], n1 = y1 * scale[j][1];
+                            const float n0 = y0 * c0, n1 = y1 * c1;
                             x[i][j][0] = n0;
                             x[i][j][1] = n1;
                             C::store2(qc + o[j] + i * P, y0 - n0, y1 - n1);
                         }
                 } else {
-                    // window scale sw: a power of two with |q_i| / sw <= 2^15 (FP16
-                    // holds up to 65504), from |q_i| <= |q_s|_2 = (1 - scale) sqrt(t)
-                    float sw[2], inv[2];
-#pragma unroll
-                    for (int e = 0; e < 2; ++e) {
-                        sw[e] = 0.f;
-                        inv[e] = 0.f;
-                        if (on[j][e]) {
-                            const float t = tsv[j][e];
-                            const float qn = (1.f - scale[j][e]) * (t * rsqrtf(t));
-                            int ex;
-                            const float sw_e = pow2_above(qn, -14, ex);
-                            if (sw_e > 0.f) {
-                                sw[e] = sw_e;
-                                inv[e] = __uint_as_float((unsigned)(127 + 14 - ex) << 23);
-                            }
-                        }
-                    }
                     // q_i / sw = y_i (1 - scale) / sw, rounded to the 16-bit type
-                    const float f0 = (1.f - scale[j][0]) * inv[0], f1 = (1.f - scale[j][1]) * inv[1];
+                    const float f0 = WinData<MIXED>::f(wf[j][0]), f1 = WinData<MIXED>::f(wf[j][1]);
+                    const float sw0 = WinData<MIXED>::sw(wf[j][0]), sw1 = WinData<MIXED>::sw(wf[j][1]);
 #pragma unroll
                     for (int i = 0; i < LB; ++i)
                         if (i < L) {
                             const float y0 = x[i][j][0], y1 = x[i][j][1];
                             const float2 h = C::store2(qc + o[j] + i * P, y0 * f0, y1 * f1);
-                            x[i][j][0] = fmaf(-h.x, sw[0], y0);   // consistent: x = y - deq(q_s)
-                            x[i][j][1] = fmaf(-h.y, sw[1], y1);
+                            x[i][j][0] = fmaf(-h.x, sw0, y0);   // consistent: x = y - deq(q_s)
+                            x[i][j][1] = fmaf(-h.y, sw1, y1);
                         }
-                    if (on[j][0] && rr[j] == 0) sc[so[j] + vv[j]] = sw[0];
-                    if (on[j][1] && r1[j] == 0) sc[so[j] + w1[j]] = sw[1];
+                    if (on[j][0] && rr[j] == 0) sc[so[j] + vv[j]] = sw0;
+                    if (on[j][1] && r1[j] == 0) sc[so[j] + w1[j]] = sw1;
                 }
             }
             fence_proxy_async_smem();   // the chunk's new contents, for the bulk store

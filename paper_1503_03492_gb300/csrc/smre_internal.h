@@ -176,7 +176,7 @@ struct BDecideArgs {
 // q element type of a batch: 0 FP32, 1 BF16, 2 FP16
 int batch_lb(int L);                       // kernel variant of side L (L itself up to 12, then 16)
 int batch_virtual_width(int L);            // columns one item may span
-size_t batch_part_bytes(int L);            // shared memory of the window sums
+size_t batch_part_bytes(int L, int qtype);            // shared memory of the window sums
 int batch_threads();
 cudaError_t batch_prepare(int qtype, size_t smem_max);
 cudaError_t launch_batch_step(int qtype, const BStepArgs &A, int grid, size_t smem,
