@@ -374,9 +374,11 @@ smre_status smre_batch_create(const smre_batch_params *p, void *cuda_stream, smr
     CREATE_CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     b->smem = (size_t)optin - 1024;   // leave room for the kernel's static shared memory
     // the ring must hold the largest block of any step
+    const size_t esz = b->qtype == SMRE_Q_FP32 ? 4 : 2;
     for (int L : sides) {
         const size_t ring = b->smem - 256 - batch_part_bytes(L, b->qtype);
-        const size_t need = (size_t)L * batch_virtual_width(L) * 4;
+        const size_t vw = batch_virtual_width(L);
+        const size_t need = std::max(L * vw * 4, L * vw * esz + (b->qtype == SMRE_Q_FP32 ? 0 : vw * 4));
         if (need > ring) {
             bfail(b, SMRE_EINVAL, "side %d: block of %zu bytes above the %zu-byte ring", L, need, ring);
             return bail(SMRE_EINVAL);

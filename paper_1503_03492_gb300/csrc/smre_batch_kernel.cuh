@@ -226,17 +226,26 @@ __device__ inline bool wait_phase(uint64_t *bar, unsigned parity, const BStepArg
     return false;
 }
 
-// Producer: walks the CTA's items in the consumers' order and fills the ring
-// with, per item, the x block and one increment block per pass.  In an
-// image's first cycle the increments are zero: their blocks are only space
-// for the consumers' results, nothing is read.
-template <typename QT>
+// Chunks in the ring have a fixed row stride: row i of an item's block sits at
+// element i * VW of the chunk, and unit s of the item occupies columns
+// s * pitch .. s * pitch + pitch - 1 of every row, so a consumer's column pair
+// is at a compile-time offset in every row.  The producer and the storer move
+// each (unit, row) of a block with its own bulk copy, spread over their lanes.
+
+// Producer warp: walks the CTA's items in the consumers' order and fills the
+// ring with, per item, the x block and one increment block per pass (plus the
+// window scales of 16-bit increments).  In an image's first cycle the
+// increments are zero: their blocks are only space for the consumers' results
+// and nothing is read.  Lane 0 keeps the ring; every lane issues copies.
+template <typename QT, int VW>
 __device__ void produce(const BStepArgs &A, unsigned char *ring, uint64_t *full,
                         uint64_t *written, int *s_off, volatile int *s_abort)
 {
     constexpr bool MIXED = QConv<QT>::mixed;
+    constexpr int esz = (int)sizeof(QT);
+    const int lane = threadIdx.x & 31;
     const int L = A.L;
-    int head = 0, d_next = 0, d_tail = 0, n_out = 0;
+    int head = 0, d_next = 0, d_tail = 0, n_out = 0;   // lane 0's view of the ring
     unsigned wph = 0;    // parity of the next `written` wait, per descriptor
     unsigned fiss = 0;   // toggled per issue: parity of the latest `full` phase, per descriptor
     bool dead = false;
@@ -269,24 +278,29 @@ __device__ void produce(const BStepArgs &A, unsigned char *ring, uint64_t *full,
             if (!pop()) return false;
         }
     };
-    // one chunk of n bytes; b0 (+ b1) bytes copied from src0 (and src1) when load
-    auto issue = [&](int n, bool load, const void *src0, unsigned b0, const void *src1,
-                     unsigned b1) -> bool {
-        int at;
-        if (!alloc(round128(n), at)) return false;
-        s_off[d_next] = at;
-        if (load) {
-            mbar_arrive_expect_tx(&full[d_next], b0 + b1);
-            bulk_load(ring + at, src0, b0, &full[d_next]);
-            if (b1) bulk_load(ring + at + round16((int)b0), src1, b1, &full[d_next]);
-        } else {
-            mbar_arrive(&full[d_next]);
+    // a chunk of n bytes whose copies will bring tx bytes (0: nothing is
+    // copied); lane 0 places it and arms its barrier, all lanes learn where
+    auto begin = [&](int n, unsigned tx, int &at, int &d) -> bool {
+        int ok = 1;
+        at = 0;
+        d = 0;
+        if (lane == 0) {
+            ok = alloc(round128(n), at) ? 1 : 0;
+            if (ok) {
+                s_off[d_next] = at;
+                if (tx) mbar_arrive_expect_tx(&full[d_next], tx);
+                else mbar_arrive(&full[d_next]);
+                fiss ^= 1u << d_next;
+                head = at + round128(n);
+                ++n_out;
+                d = d_next;
+                d_next = d_next + 1 == kD ? 0 : d_next + 1;
+            }
         }
-        fiss ^= 1u << d_next;
-        head = at + round128(n);
-        ++n_out;
-        d_next = d_next + 1 == kD ? 0 : d_next + 1;
-        return true;
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        at = __shfl_sync(0xffffffffu, at, 0);
+        d = __shfl_sync(0xffffffffu, d, 0);
+        return ok != 0;
     };
 
     for (int item = blockIdx.x; item < A.n_items && !dead; item += gridDim.x) {
@@ -295,24 +309,40 @@ __device__ void produce(const BStepArgs &A, unsigned char *ring, uint64_t *full,
         if (im.ctl->stop) continue;
         const int P = im.pitch;
         const bool first = im.ctl->cycles == 0;
-        const unsigned xbytes = (unsigned)(it.nu * L * P) * 4u;
-        if (!issue((int)xbytes, true, im.x + (size_t)(A.a + L * it.u0) * P, xbytes, nullptr, 0)) {
+        const int rows = it.nu * L;   // row r = unit r / L, row r % L of it
+        int at, d;
+        if (!begin(L * VW * 4, (unsigned)(rows * P) * 4u, at, d)) {
             dead = true;
             break;
         }
-        const unsigned qbytes = (unsigned)(it.nu * L * P) * (unsigned)sizeof(QT);
+        const float *xsrc = im.x + (size_t)(A.a + L * it.u0) * P;
+        for (int r = lane; r < rows; r += 32) {
+            const int s = r / L, i = r - s * L;
+            bulk_load(ring + at + (size_t)(i * VW + s * P) * 4, xsrc + (size_t)r * P,
+                      (unsigned)P * 4u, &full[d]);
+        }
         const int nwp = scale_row(im.W, L);
-        const unsigned sbytes = MIXED ? (unsigned)(it.nu * nwp) * 4u : 0u;
+        const unsigned tx = first ? 0u
+                                  : (unsigned)(rows * P * esz) + (MIXED ? (unsigned)(it.nu * nwp) * 4u : 0u);
         for (int b = 0; b < L; ++b) {
-            const QT *qsrc = reinterpret_cast<const QT *>(im.q) + im.qoff[A.p0 + b] +
-                             (size_t)it.u0 * L * P;
-            const float *ssrc = MIXED ? im.qs + im.soff[A.p0 + b] + (size_t)it.u0 * nwp : nullptr;
-            if (!issue(round16((int)qbytes) + (int)sbytes, !first, qsrc, qbytes, ssrc, sbytes)) {
+            if (!begin(L * VW * esz + (MIXED ? VW * 4 : 0), tx, at, d)) {
                 dead = true;
                 break;
             }
+            if (first) continue;
+            const QT *qsrc = reinterpret_cast<const QT *>(im.q) + im.qoff[A.p0 + b] +
+                             (size_t)it.u0 * L * P;
+            for (int r = lane; r < rows; r += 32) {
+                const int s = r / L, i = r - s * L;
+                bulk_load(ring + at + (size_t)(i * VW + s * P) * esz, qsrc + (size_t)r * P,
+                          (unsigned)(P * esz), &full[d]);
+            }
+            if (MIXED && lane == 0)
+                bulk_load(ring + at + (size_t)L * VW * esz, im.qs + im.soff[A.p0 + b] + (size_t)it.u0 * nwp,
+                          (unsigned)(it.nu * nwp) * 4u, &full[d]);
         }
     }
+    if (lane != 0) return;
     if (!dead) {
         while (n_out > 0)
             if (!pop()) { dead = true; break; }
@@ -327,14 +357,17 @@ __device__ void produce(const BStepArgs &A, unsigned char *ring, uint64_t *full,
     }
 }
 
-// Storer: once the consumers have written a pass's new increments (and
-// scales) into its chunk, copies the chunk to the increment plane with bulk
-// stores and releases it to the producer when the copy has read it.
-template <typename QT>
+// Storer warp: once the consumers have written a pass's new increments (and
+// scales) into its chunk, copies each (unit, row) of the chunk to the
+// increment plane with bulk stores and releases the chunk to the producer
+// when every copy has read it.
+template <typename QT, int VW>
 __device__ void store_back(const BStepArgs &A, unsigned char *ring, uint64_t *written,
                            uint64_t *ready, const int *s_off, volatile int *s_abort)
 {
     constexpr bool MIXED = QConv<QT>::mixed;
+    constexpr int esz = (int)sizeof(QT);
+    const int lane = threadIdx.x & 31;
     const int L = A.L;
     int ds = 0;
     unsigned rph = 0;   // parity of the next `ready` wait, per descriptor
@@ -344,24 +377,30 @@ __device__ void store_back(const BStepArgs &A, unsigned char *ring, uint64_t *wr
         if (im.ctl->stop) continue;
         const int P = im.pitch;
         const int nwp = scale_row(im.W, L);
-        const unsigned qbytes = (unsigned)(it.nu * L * P) * (unsigned)sizeof(QT);
-        const unsigned sbytes = MIXED ? (unsigned)(it.nu * nwp) * 4u : 0u;
+        const int rows = it.nu * L;
         ds = ds + 1 == kD ? 0 : ds + 1;   // the x chunk: released by the consumers
         for (int b = 0; b < L; ++b) {
-            if (!wait_phase(&ready[ds], (rph >> ds) & 1u, A, s_abort)) {
+            int ok = 1;
+            if (lane == 0) ok = wait_phase(&ready[ds], (rph >> ds) & 1u, A, s_abort) ? 1 : 0;
+            if (!__shfl_sync(0xffffffffu, ok, 0)) {
                 bulk_wait_all();
                 return;
             }
             rph ^= 1u << ds;
             const unsigned char *src = ring + s_off[ds];
-            bulk_store(reinterpret_cast<QT *>(im.q) + im.qoff[A.p0 + b] + (size_t)it.u0 * L * P,
-                       src, qbytes);
-            if (MIXED)
-                bulk_store(im.qs + im.soff[A.p0 + b] + (size_t)it.u0 * nwp, src + round16((int)qbytes),
-                           sbytes);
+            QT *qdst = reinterpret_cast<QT *>(im.q) + im.qoff[A.p0 + b] + (size_t)it.u0 * L * P;
+            for (int r = lane; r < rows; r += 32) {
+                const int s = r / L, i = r - s * L;
+                bulk_store(qdst + (size_t)r * P, src + (size_t)(i * VW + s * P) * esz,
+                           (unsigned)(P * esz));
+            }
+            if (MIXED && lane == 0)
+                bulk_store(im.qs + im.soff[A.p0 + b] + (size_t)it.u0 * nwp, src + (size_t)L * VW * esz,
+                           (unsigned)(it.nu * nwp) * 4u);
             bulk_commit();
             bulk_wait_read0();
-            mbar_arrive_cnt(&written[ds], kNCW);
+            __syncwarp();
+            if (lane == 0) mbar_arrive_cnt(&written[ds], kNCW);
             ds = ds + 1 == kD ? 0 : ds + 1;
         }
     }
@@ -405,11 +444,11 @@ __global__ void __launch_bounds__(kThreads, 1) bstep_kernel(const BStepArgs A)
     __syncthreads();
 
     if (warp == kNCW) {
-        if (lane == 0) produce<QT>(A, ring, full, written, s_off, &s_abort);
+        produce<QT, VW>(A, ring, full, written, s_off, &s_abort);
         return;
     }
     if (warp == kNCW + 1) {
-        if (lane == 0) store_back<QT>(A, ring, written, ready, s_off, &s_abort);
+        store_back<QT, VW>(A, ring, written, ready, s_off, &s_abort);
         return;
     }
 
@@ -429,34 +468,35 @@ __global__ void __launch_bounds__(kThreads, 1) bstep_kernel(const BStepArgs A)
         // column-sum slot; so: its unit's scale row; (vv, rr): window of column
         // c in the current pass and c's place in it, advanced each pass.
         // Columns outside the item get a window index that never lies in a pass.
-        int o[CPP], po[CPP], so[CPP], vv[CPP], rr[CPP];
+        int og[CPP], so[CPP], vv[CPP], rr[CPP];
 #pragma unroll
         for (int j = 0; j < CPP; ++j) {
             const int vc = 2 * (tid + kNC * j);
             const int sj = vc / P;
             const int c = vc - sj * P;
-            o[j] = sj * L * P + c;
-            po[j] = sj * P + c;
+            og[j] = sj * L * P + c;   // row 0 of the pair in the image rows of the item
             so[j] = sj * nwp;
             vv[j] = sj < it.nu && c < W ? c / L : kOutside;
             rr[j] = c % L;
         }
+        // this thread's first pair in a chunk row and in the column sums; pair j
+        // and row i lie at the compile-time offset i VW + 2 kNC j from there
+        const int vc0 = 2 * tid;
 
         // the item's rows of x into registers
-        float x[LB][CPP][2];
+        float2 x[LB][CPP];   // (column c, column c + 1); pairs use the FP32x2 arithmetic
         bool bad = !wait_phase(&full[dc], (fph >> dc) & 1u, A, &s_abort);
         fph ^= 1u << dc;
         {
-            const float *xb = reinterpret_cast<const float *>(ring + s_off[dc]);
+            const float *xb = reinterpret_cast<const float *>(ring + s_off[dc]) + vc0;
 #pragma unroll
             for (int j = 0; j < CPP; ++j)
 #pragma unroll
                 for (int i = 0; i < LB; ++i) {
                     float2 v = make_float2(0.f, 0.f);
                     if (i < L && vv[j] >= 0 && !bad)
-                        v = *reinterpret_cast<const float2 *>(xb + o[j] + i * P);
-                    x[i][j][0] = v.x;
-                    x[i][j][1] = v.y;
+                        v = *reinterpret_cast<const float2 *>(xb + i * VW + 2 * kNC * j);
+                    x[i][j] = v;
                 }
         }
         __syncwarp();
@@ -469,8 +509,8 @@ __global__ void __launch_bounds__(kThreads, 1) bstep_kernel(const BStepArgs A)
             if (!bad) bad = !wait_phase(&full[dc], (fph >> dc) & 1u, A, &s_abort);
             fph ^= 1u << dc;
             unsigned char *chunk = ring + s_off[dc];
-            QT *qc = reinterpret_cast<QT *>(chunk);   // qc[o + i P]: row i of the pair
-            float *sc = reinterpret_cast<float *>(chunk + round16(it.nu * L * P * (int)sizeof(QT)));
+            QT *qc = reinterpret_cast<QT *>(chunk) + vc0;   // qc[i VW + 2 kNC j]: row i of pair j
+            float *sc = reinterpret_cast<float *>(chunk + (size_t)L * VW * sizeof(QT));
             // windows of both columns of each pair
             int w1[CPP], r1[CPP];
             bool on[CPP][2];
@@ -485,31 +525,23 @@ __global__ void __launch_bounds__(kThreads, 1) bstep_kernel(const BStepArgs A)
 #pragma unroll
             for (int j = 0; j < CPP; ++j) {
                 if (!(on[j][0] || on[j][1]) || bad) continue;
-                float s0 = 1.f, s1 = 1.f;
+                float2 s2 = make_float2(1.f, 1.f);   // dequantisation scales of the pair
                 if (MIXED && !first) {
-                    s0 = on[j][0] ? sc[so[j] + vv[j]] : 0.f;
-                    s1 = on[j][1] ? sc[so[j] + w1[j]] : 0.f;
+                    s2.x = on[j][0] ? sc[so[j] + vv[j]] : 0.f;
+                    s2.y = on[j][1] ? sc[so[j] + w1[j]] : 0.f;
                 }
-                float sq0 = 0.f, sq1 = 0.f;
+                float2 sq = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int i = 0; i < LB; ++i) {
                     if (i < L) {
-                        float2 qv = make_float2(0.f, 0.f);
                         if (!first) {
-                            qv = C::load2(qc + o[j] + i * P);
-                            if (MIXED) {
-                                qv.x *= s0;
-                                qv.y *= s1;
-                            }
+                            const float2 qv = C::load2(qc + i * VW + 2 * kNC * j);
+                            x[i][j] = MIXED ? __ffma2_rn(qv, s2, x[i][j]) : __fadd2_rn(x[i][j], qv);
                         }
-                        const float y0 = x[i][j][0] + qv.x, y1 = x[i][j][1] + qv.y;
-                        x[i][j][0] = y0;
-                        x[i][j][1] = y1;
-                        sq0 = fmaf(y0, y0, sq0);
-                        sq1 = fmaf(y1, y1, sq1);
+                        sq = __ffma2_rn(x[i][j], x[i][j], sq);
                     }
                 }
-                *reinterpret_cast<float2 *>(part + po[j]) = make_float2(sq0, sq1);
+                *reinterpret_cast<float2 *>(part + vc0 + 2 * kNC * j) = sq;
             }
             if (named_sync_or(1, bad, kNC)) {   // column sums complete (or a copy was lost)
                 aborted = true;
@@ -530,7 +562,7 @@ __global__ void __launch_bounds__(kThreads, 1) bstep_kernel(const BStepArgs A)
                 for (int e = 0; e < 2; ++e) {
                     tl[j][e] = 0.f;
                     if (!on[j][e] || (e ? r1[j] : rr[j]) != 0) continue;
-                    const float *pp = part + po[j] + e;
+                    const float *pp = part + vc0 + 2 * kNC * j + e;
                     float pv[LB];
 #pragma unroll
                     for (int m = 0; m < LB; ++m) pv[m] = m < L ? pp[m] : 0.f;
@@ -540,7 +572,7 @@ __global__ void __launch_bounds__(kThreads, 1) bstep_kernel(const BStepArgs A)
                         if (m < L) ts += pv[m];
                     tl[j][e] = ts;
                     if (fabsf(ts - cS) <= kNearBand * cS) near = true;
-                    wdat[po[j] + e] = window_factors<MIXED>(ts, cS, sqrt_cS, 0.0, 0.0, false);
+                    wdat[vc0 + 2 * kNC * j + e] = window_factors<MIXED>(ts, cS, sqrt_cS, 0.0, 0.0, false);
                 }
             if (named_sync_or(1, near, kNC)) {
                 // rare: windows within the band get their sums again in FP64
@@ -552,8 +584,11 @@ __global__ void __launch_bounds__(kThreads, 1) bstep_kernel(const BStepArgs A)
                         if (on[j][e]) {
 #pragma unroll
                             for (int i = 0; i < LB; ++i)
-                                if (i < L) s64 = fma((double)x[i][j][e], (double)x[i][j][e], s64);
-                            part64[po[j] + e] = s64;
+                                if (i < L) {
+                                    const double v = e ? x[i][j].y : x[i][j].x;
+                                    s64 = fma(v, v, s64);
+                                }
+                            part64[vc0 + 2 * kNC * j + e] = s64;
                         }
                     }
                 named_sync(1, kNC);
@@ -564,8 +599,8 @@ __global__ void __launch_bounds__(kThreads, 1) bstep_kernel(const BStepArgs A)
                         if (!on[j][e] || (e ? r1[j] : rr[j]) != 0) continue;
                         if (fabsf(tl[j][e] - cS) > kNearBand * cS) continue;
                         double t64 = 0.0;
-                        for (int m = 0; m < L; ++m) t64 += part64[po[j] + e + m];
-                        wdat[po[j] + e] = window_factors<MIXED>((float)t64, cS, sqrt_cS, t64, A.cS64,
+                        for (int m = 0; m < L; ++m) t64 += part64[vc0 + 2 * kNC * j + e + m];
+                        wdat[vc0 + 2 * kNC * j + e] = window_factors<MIXED>((float)t64, cS, sqrt_cS, t64, A.cS64,
                                                                 true);
                     }
                 named_sync(1, kNC);
@@ -576,7 +611,7 @@ __global__ void __launch_bounds__(kThreads, 1) bstep_kernel(const BStepArgs A)
             for (int j = 0; j < CPP; ++j)
 #pragma unroll
                 for (int e = 0; e < 2; ++e)
-                    wf[j][e] = on[j][e] ? wdat[po[j] + e - (e ? r1[j] : rr[j])]
+                    wf[j][e] = on[j][e] ? wdat[vc0 + 2 * kNC * j + e - (e ? r1[j] : rr[j])]
                                         : WinData<MIXED>::none();
 
             // x = p_s(y), q_s = y - x; the new increments go into the chunk,
@@ -585,27 +620,29 @@ __global__ void __launch_bounds__(kThreads, 1) bstep_kernel(const BStepArgs A)
             for (int j = 0; j < CPP; ++j) {
                 if (!(on[j][0] || on[j][1])) continue;
                 if (!MIXED) {
-                    const float c0 = WinData<MIXED>::scale(wf[j][0]), c1 = WinData<MIXED>::scale(wf[j][1]);
+                    const float2 c2 = make_float2(WinData<MIXED>::scale(wf[j][0]),
+                                                  WinData<MIXED>::scale(wf[j][1]));
 #pragma unroll
                     for (int i = 0; i < LB; ++i)
                         if (i < L) {
-                            const float y0 = x[i][j][0], y1 = x[i][j][1];
-                            const float n0 = y0 * c0, n1 = y1 * c1;
-                            x[i][j][0] = n0;
-                            x[i][j][1] = n1;
-                            C::store2(qc + o[j] + i * P, y0 - n0, y1 - n1);
+                            const float2 y = x[i][j];
+                            const float2 n = __fmul2_rn(y, c2);
+                            x[i][j] = n;
+                            const float2 q = __fadd2_rn(y, make_float2(-n.x, -n.y));
+                            C::store2(qc + i * VW + 2 * kNC * j, q.x, q.y);
                         }
                 } else {
                     // q_i / sw = y_i (1 - scale) / sw, rounded to the 16-bit type
-                    const float f0 = WinData<MIXED>::f(wf[j][0]), f1 = WinData<MIXED>::f(wf[j][1]);
+                    const float2 f2 = make_float2(WinData<MIXED>::f(wf[j][0]), WinData<MIXED>::f(wf[j][1]));
                     const float sw0 = WinData<MIXED>::sw(wf[j][0]), sw1 = WinData<MIXED>::sw(wf[j][1]);
+                    const float2 nsw = make_float2(-sw0, -sw1);
 #pragma unroll
                     for (int i = 0; i < LB; ++i)
                         if (i < L) {
-                            const float y0 = x[i][j][0], y1 = x[i][j][1];
-                            const float2 h = C::store2(qc + o[j] + i * P, y0 * f0, y1 * f1);
-                            x[i][j][0] = fmaf(-h.x, sw0, y0);   // consistent: x = y - deq(q_s)
-                            x[i][j][1] = fmaf(-h.y, sw1, y1);
+                            const float2 y = x[i][j];
+                            const float2 v = __fmul2_rn(y, f2);
+                            const float2 h = C::store2(qc + i * VW + 2 * kNC * j, v.x, v.y);
+                            x[i][j] = __ffma2_rn(h, nsw, y);   // consistent: x = y - deq(q_s)
                         }
                     if (on[j][0] && rr[j] == 0) sc[so[j] + vv[j]] = sw0;
                     if (on[j][1] && r1[j] == 0) sc[so[j] + w1[j]] = sw1;
@@ -633,8 +670,7 @@ __global__ void __launch_bounds__(kThreads, 1) bstep_kernel(const BStepArgs A)
 #pragma unroll
                 for (int i = 0; i < LB; ++i)
                     if (i < L)
-                        *reinterpret_cast<float2 *>(xg + o[j] + i * P) =
-                            make_float2(x[i][j][0], x[i][j][1]);
+                        *reinterpret_cast<float2 *>(xg + og[j] + i * P) = x[i][j];
             }
     }
 }
