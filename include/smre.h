@@ -76,6 +76,11 @@ typedef enum {
                                      (side, row offset) group with a host-side stop
                                      check per cycle, instead of the single persistent
                                      cooperative launch (same results, slower)        */
+#define SMRE_F_AUTOTUNE 8         /* at create, time three cycles of every schedule that
+                                     can run the shape (persistent launch, one-image
+                                     batch, group launches) on a seeded test image and
+                                     keep the fastest; cached per (device, H, W, sides,
+                                     q_dtype) for the process                         */
 #define SMRE_F_SELFTEST_TIMEOUT 4 /* testing aid: the persistent launch additionally
                                      waits on a flag nothing sets, with a 50 ms limit,
                                      so smre_dykstra_project must return
@@ -174,6 +179,12 @@ SMRE_API smre_status smre_dykstra_history(smre_dykstra *h, double *out, int n_ma
  * pass by pass (i = 0..K), tiles row-major within a pass.  *n_tiles receives
  * the total; at most n_max values are copied. */
 SMRE_API smre_status smre_dykstra_icd_sweeps(smre_dykstra *h, int *out, int n_max, int *n_tiles);
+
+/* How the handle runs the standard method: */
+#define SMRE_SCHED_PERSISTENT 1   /* one persistent cooperative launch per projection */
+#define SMRE_SCHED_BATCHED 2      /* a one-image batch: one step launch per group     */
+#define SMRE_SCHED_GROUPS 3       /* one group-kernel launch per group, host stop check */
+SMRE_API int smre_dykstra_schedule(const smre_dykstra *h);
 
 /* Number of kernels the handle has launched since it was created (every
  * launch of every entry point; a monotone counter kept on the host). */

@@ -19,7 +19,8 @@ import os
 __all__ = [
     "SMRE_OK", "SMRE_EINVAL", "SMRE_ENOMEM", "SMRE_ECUDA", "SMRE_ETIMEOUT", "SMRE_ENOTCONVERGED",
     "SMRE_C_PERSET", "SMRE_C_CHI2", "SMRE_C_MAXSTAT", "SMRE_C_EXPLICIT", "SMRE_F_VIOLATION",
-    "SMRE_F_GROUP_LAUNCHES", "SMRE_F_SELFTEST_TIMEOUT",
+    "SMRE_F_GROUP_LAUNCHES", "SMRE_F_SELFTEST_TIMEOUT", "SMRE_F_AUTOTUNE", "SMRE_SCHED_PERSISTENT",
+    "SMRE_SCHED_BATCHED", "SMRE_SCHED_GROUPS", "smre_dykstra_schedule",
     "SmreError", "smre_params", "smre_result", "lib_path", "load",
     "smre_bounds", "smre_dykstra_create", "smre_dykstra_project",
     "smre_dykstra_project_incomplete", "smre_dykstra_set_stopping", "smre_dykstra_bounds",
@@ -40,6 +41,8 @@ SMRE_C_PERSET, SMRE_C_CHI2, SMRE_C_MAXSTAT, SMRE_C_EXPLICIT = range(4)
 SMRE_F_VIOLATION = 1
 SMRE_F_GROUP_LAUNCHES = 2
 SMRE_F_SELFTEST_TIMEOUT = 4
+SMRE_F_AUTOTUNE = 8
+SMRE_SCHED_PERSISTENT, SMRE_SCHED_BATCHED, SMRE_SCHED_GROUPS = 1, 2, 3
 SMRE_Q_FP32, SMRE_Q_BF16, SMRE_Q_FP16 = range(3)
 
 _STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENOTCONVERGED"}
@@ -50,7 +53,8 @@ EXPORTED = (
     "smre_dykstra_project_incomplete", "smre_dykstra_set_stopping", "smre_dykstra_bounds",
     "smre_dykstra_history", "smre_dykstra_icd_sweeps", "smre_dykstra_device_bytes",
     "smre_dykstra_destroy", "smre_last_error", "smre_version", "smre_dykstra_kernel_launches",
-    "smre_dykstra_project_static", "smre_batch_image_bytes", "smre_batch_create",
+    "smre_dykstra_project_static", "smre_dykstra_schedule", "smre_batch_image_bytes",
+    "smre_batch_create",
     "smre_batch_submit", "smre_batch_run", "smre_batch_poll", "smre_batch_retrieve",
     "smre_batch_project", "smre_batch_active", "smre_batch_kernel_launches",
     "smre_batch_device_bytes", "smre_batch_last_error", "smre_batch_destroy",
@@ -152,6 +156,7 @@ def load():
         "smre_dykstra_icd_sweeps": (st, [H, P(ctypes.c_int), ctypes.c_int, P(ctypes.c_int)]),
         "smre_dykstra_device_bytes": (ctypes.c_size_t, [H]),
         "smre_dykstra_kernel_launches": (ctypes.c_longlong, [H]),
+        "smre_dykstra_schedule": (ctypes.c_int, [H]),
         "smre_dykstra_project_static": (st, [P(smre_params), ctypes.c_void_p, ctypes.c_void_p,
                                              ctypes.c_void_p, P(smre_result)]),
         "smre_dykstra_destroy": (None, [H]),
@@ -336,6 +341,11 @@ def smre_dykstra_project_static(params: smre_params, x0, x, stream=None, want_re
     return res if want_result else None
 
 
+def smre_dykstra_schedule(h) -> int:
+    """SMRE_SCHED_PERSISTENT, SMRE_SCHED_BATCHED or SMRE_SCHED_GROUPS."""
+    return int(load().smre_dykstra_schedule(h))
+
+
 def smre_dykstra_kernel_launches(h) -> int:
     return int(load().smre_dykstra_kernel_launches(h))
 
@@ -374,6 +384,9 @@ class Projector:
 
     def kernel_launches(self):
         return smre_dykstra_kernel_launches(self.h)
+
+    def schedule(self):
+        return smre_dykstra_schedule(self.h)
 
     def close(self):
         if self.h:

@@ -8,6 +8,9 @@
 #include <cstdio>
 #include <cstring>
 #include <cstdlib>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <new>
 #include <type_traits>
 #include <string>
@@ -34,6 +37,8 @@ struct smre_dykstra {
     // kernels (16-bit increments, or FP32 images too wide for the persistent
     // kernel); see use_batch
     smre_batch *bat = nullptr;
+    bool persist_ok = false;       // the persistent plan exists (it may not be the one used)
+    std::string tuned;             // "", "measured" or "cached"
     // stopping rule
     int max_cycles = 1;
     double tol = -1.0;
@@ -214,7 +219,7 @@ smre_status make_handle_batch(smre_dykstra *h)
     bp.n_sides = (int)h->sides.size();
     bp.cmode = SMRE_C_EXPLICIT;
     bp.c_explicit = h->cS.data();
-    bp.max_cycles = h->max_cycles;
+    bp.max_cycles = std::max(h->max_cycles, 3);   // room for the tuner's three cycles
     bp.tol = h->tol;
     bp.tol_relative = h->tol_relative;
     bp.q_dtype = h->q_dtype;
@@ -222,6 +227,114 @@ smre_status make_handle_batch(smre_dykstra *h)
     bp.device_bytes = smre_batch_image_bytes(&bp, h->H, h->W) + 4096;
     const smre_status st = smre_batch_create(&bp, h->stream, &h->bat);
     if (st != SMRE_OK) return fail(h, st, "one-image batch: %s", smre_batch_last_error(nullptr));
+    batch_set_rule(h->bat, h->max_cycles, h->tol, h->tol_relative);
+    return SMRE_OK;
+}
+
+// ---- schedule autotuner (SMRE_F_AUTOTUNE)
+//
+// For one problem shape the standard method can run as the persistent
+// cooperative launch, as a one-image batch (one step-kernel launch per group)
+// or as one group-kernel launch per group with a host stop check per cycle.
+// Which is fastest depends on the size and the sides, so the tuner times
+// three cycles of each applicable schedule on a seeded test image (the time of
+// a cycle hardly depends on the values) and keeps the fastest.  The choice is
+// cached per (device, H, W, sides, q_dtype) for the process.
+
+using TuneKey = std::tuple<int, int, int, std::vector<int>, int>;
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tune_cache;
+
+smre_status project_core(smre_dykstra *h, const float *x0, float *x, smre_result *res);
+
+int current_schedule(const smre_dykstra *h)
+{
+    if (h->bat) return SMRE_SCHED_BATCHED;
+    return h->persist ? SMRE_SCHED_PERSISTENT : SMRE_SCHED_GROUPS;
+}
+
+// Point the handle at schedule s (its state must exist).
+void use_schedule(smre_dykstra *h, int s, smre_batch *bat)
+{
+    h->bat = s == SMRE_SCHED_BATCHED ? bat : nullptr;
+    h->persist = s == SMRE_SCHED_PERSISTENT;
+}
+
+smre_status autotune(smre_dykstra *h)
+{
+    int dev = 0;
+    CK(h, cudaGetDevice(&dev));
+    const TuneKey key{dev, h->H, h->W, h->sides, h->q_dtype};
+    int cached = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) cached = it->second;
+    }
+    smre_batch *bat = h->bat;   // made at create when a batch can run the shape
+    std::vector<int> cand;
+    if (h->q_dtype == SMRE_Q_FP32) {
+        if (h->persist_ok) cand.push_back(SMRE_SCHED_PERSISTENT);
+        cand.push_back(SMRE_SCHED_GROUPS);
+    }
+    if (bat) cand.push_back(SMRE_SCHED_BATCHED);
+    int best = cand.empty() ? current_schedule(h) : cand[0];
+    if (cached) {
+        best = cached;
+        h->tuned = "cached";
+    } else if (cand.size() > 1) {
+        // seeded test image: uniform values in [-3, 3) (many windows violate)
+        std::vector<float> img((size_t)h->H * h->W);
+        unsigned long long z = 0x9E3779B97F4A7C15ull;
+        for (float &v : img) {
+            z = z * 6364136223846793005ull + 1442695040888963407ull;
+            v = (float)((double)(z >> 11) * (6.0 / 9007199254740992.0) - 3.0);
+        }
+        float *xt = nullptr;
+        CK(h, cudaMalloc(&xt, sizeof(float) * img.size()));
+        CK(h, cudaMemcpy(xt, img.data(), sizeof(float) * img.size(), cudaMemcpyHostToDevice));
+        const int mc = h->max_cycles;
+        const double tol = h->tol;
+        const int rel = h->tol_relative;
+        h->max_cycles = 3;
+        h->tol = -1.0;
+        if (bat) batch_set_rule(bat, 3, -1.0, 0);
+        double best_t = 1e300;
+        smre_status st = SMRE_OK;
+        for (int c : cand) {
+            use_schedule(h, c, bat);
+            smre_result r{};
+            st = project_core(h, xt, xt, &r);
+            if (st != SMRE_OK && st != SMRE_ENOTCONVERGED) break;
+            st = SMRE_OK;
+            if (r.seconds < best_t) {
+                best_t = r.seconds;
+                best = c;
+            }
+        }
+        cudaFree(xt);
+        h->max_cycles = mc;
+        h->tol = tol;
+        h->tol_relative = rel;
+        if (bat) batch_set_rule(bat, mc, tol, rel);
+        if (st != SMRE_OK) return st;
+        h->tuned = "measured";
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = best;
+    }
+    use_schedule(h, best, bat);
+    if (best != SMRE_SCHED_BATCHED && bat) {
+        smre_batch_destroy(bat);
+        h->bat = nullptr;
+    }
+    if (best == SMRE_SCHED_BATCHED && h->q_floats > 0) {
+        // the batch holds the increments: drop the handle's own store
+        cudaFree(h->q);
+        h->q = nullptr;
+        CK(h, cudaMalloc(&h->q, sizeof(float)));
+        h->dev_bytes -= sizeof(float) * (h->q_floats - 1);
+        h->q_floats = 0;
+    }
     return SMRE_OK;
 }
 
@@ -587,6 +700,7 @@ smre_status plan_persistent(smre_dykstra *h, int flags)
         if (ms > 0) h->timeout_ns = (unsigned long long)(ms * 1e6);
     }
     h->persist = true;
+    h->persist_ok = true;
     return SMRE_OK;
 }
 
@@ -628,137 +742,9 @@ smre_status run_persistent(smre_dykstra *h)
     return SMRE_OK;
 }
 
-}  // namespace
 
-namespace smre {
-void set_thread_error(const char *msg) { g_err = msg; }
-}  // namespace smre
-
-extern "C" {
-
-const char *smre_version(void) { return "smre-gb300 0.3 (sm_103a)"; }
-
-const char *smre_last_error(const smre_dykstra *h)
+smre_status project_core(smre_dykstra *h, const float *x0, float *x, smre_result *res)
 {
-    if (h) return h->err.c_str();
-    return g_err.c_str();
-}
-
-smre_status smre_bounds(const smre_params *p, double *cS_out)
-{
-    std::vector<int> sides;
-    std::vector<double> cexp, cS;
-    smre_status st = check_params(p, sides, cexp);
-    if (st != SMRE_OK) return st;
-    if (!cS_out) return fail(nullptr, SMRE_EINVAL, "cS_out is NULL");
-    st = compute_bounds(p, sides, cexp, cS);
-    if (st != SMRE_OK) return st;
-    for (int i = 0; i < p->n_sides; ++i) {
-        const int L = p->sides[i];
-        const size_t j = std::lower_bound(sides.begin(), sides.end(), L) - sides.begin();
-        cS_out[i] = cS[j];
-    }
-    return SMRE_OK;
-}
-
-smre_status smre_dykstra_create(const smre_params *p, void *cuda_stream, smre_dykstra **out)
-{
-    if (!out) return fail(nullptr, SMRE_EINVAL, "out is NULL");
-    *out = nullptr;
-    std::vector<int> sides;
-    std::vector<double> cexp;
-    smre_status st = check_params(p, sides, cexp);
-    if (st != SMRE_OK) return st;
-    smre_dykstra *h = new (std::nothrow) smre_dykstra();
-    if (!h) return fail(nullptr, SMRE_ENOMEM, "host allocation failed");
-    h->H = p->height;
-    h->W = p->width;
-    h->pitch = round_up(p->width, 32);
-    h->sides = sides;
-    h->cmode = p->cmode;
-    h->alpha = p->alpha;
-    h->maxstat_draws = p->maxstat_draws ? p->maxstat_draws : 1000;
-    h->seed = p->seed;
-    h->flags = p->flags;
-    h->max_ctas = p->max_ctas;
-    h->q_dtype = p->q_dtype;
-    h->max_cycles = p->max_cycles;
-    h->tol = p->tol;
-    h->tol_relative = p->tol_relative ? 1 : 0;
-    h->icd_max_sweeps = p->icd_max_sweeps ? p->icd_max_sweeps : 1000;
-    h->stream = (cudaStream_t)cuda_stream;
-
-    st = compute_bounds(p, sides, cexp, h->cS);
-    if (st != SMRE_OK) {
-        delete h;
-        return st;
-    }
-    for (size_t i = 0; i < sides.size(); ++i) h->cS_of[sides[i]] = h->cS[i];
-    build_schedule(h);
-    const bool batched = use_batch(p, sides.back());
-    if (batched) h->q_floats = 0;   // the batch holds the increments
-
-    auto bail = [&](smre_status s2) {
-        g_err = h->err;
-        smre_dykstra_destroy(h);
-        return s2;
-    };
-#define CKC(call)                                                                         \
-    do {                                                                                  \
-        cudaError_t e_ = (call);                                                          \
-        if (e_ != cudaSuccess) {                                                          \
-            fail(h, e_ == cudaErrorMemoryAllocation ? SMRE_ENOMEM : SMRE_ECUDA, "%s: %s", \
-                 #call, cudaGetErrorString(e_));                                          \
-            return bail(e_ == cudaErrorMemoryAllocation ? SMRE_ENOMEM : SMRE_ECUDA);     \
-        }                                                                                 \
-    } while (0)
-
-    const size_t img = sizeof(float) * (size_t)h->H * h->pitch;
-    CKC(cudaMalloc(&h->q, sizeof(float) * std::max<size_t>(h->q_floats, 1)));
-    CKC(cudaMalloc(&h->xw, img));
-    CKC(cudaMalloc(&h->xprev, img));
-    CKC(cudaMemset(h->xw, 0, img));
-    CKC(cudaMemset(h->xprev, 0, img));
-    h->n_partials = norm_blocks();
-    CKC(cudaMalloc(&h->partials, sizeof(double) * 2 * h->n_partials));
-    CKC(cudaMalloc(&h->ctl, sizeof(Control)));
-    CKC(cudaMalloc(&h->viol, sizeof(double)));
-    CKC(cudaMallocHost(&h->ctl_host, sizeof(Control)));
-    CKC(cudaMallocHost(&h->viol_host, sizeof(double)));
-    CKC(cudaEventCreate(&h->ev0));
-    CKC(cudaEventCreate(&h->ev1));
-    h->dev_bytes = sizeof(float) * std::max<size_t>(h->q_floats, 1) + 2 * img +
-                   sizeof(double) * 2 * h->n_partials + sizeof(Control) + sizeof(double);
-    if (ensure_hist(h, h->max_cycles) != SMRE_OK) return bail(SMRE_ENOMEM);
-    if (batched) {
-        st = make_handle_batch(h);
-        if (st != SMRE_OK) return bail(st);
-    } else if (plan_persistent(h, p->flags) != SMRE_OK) {
-        return bail(SMRE_ECUDA);
-    }
-#undef CKC
-    *out = h;
-    return SMRE_OK;
-}
-
-smre_status smre_dykstra_set_stopping(smre_dykstra *h, int max_cycles, double tol, int tol_relative)
-{
-    if (!h) return fail(nullptr, SMRE_EINVAL, "handle is NULL");
-    if (max_cycles < 1) return fail(h, SMRE_EINVAL, "max_cycles must be >= 1");
-    if (std::isnan(tol)) return fail(h, SMRE_EINVAL, "tol is NaN");
-    smre_status st = ensure_hist(h, max_cycles);
-    if (st != SMRE_OK) return st;
-    h->max_cycles = max_cycles;
-    h->tol = tol;
-    h->tol_relative = tol_relative ? 1 : 0;
-    if (h->bat && batch_set_rule(h->bat, max_cycles, tol, tol_relative) != SMRE_OK)
-        return make_handle_batch(h);   // more cycles than its history holds: a new batch
-    return SMRE_OK;
-}
-
-smre_status smre_dykstra_project(smre_dykstra *h, const float *x0, float *x, smre_result *res)
-{
-    if (!h) return fail(nullptr, SMRE_EINVAL, "handle is NULL");
     if (!x0 || !x) return fail(h, SMRE_EINVAL, "x0 / x is NULL");
     smre_status st = stage_in(h, x0);
     if (st != SMRE_OK) return st;
@@ -839,6 +825,155 @@ smre_status smre_dykstra_project(smre_dykstra *h, const float *x0, float *x, smr
     }
     return SMRE_OK;
 }
+
+}  // namespace
+
+namespace smre {
+void set_thread_error(const char *msg) { g_err = msg; }
+}  // namespace smre
+
+extern "C" {
+
+const char *smre_version(void) { return "smre-gb300 0.3 (sm_103a)"; }
+
+const char *smre_last_error(const smre_dykstra *h)
+{
+    if (h) return h->err.c_str();
+    return g_err.c_str();
+}
+
+smre_status smre_bounds(const smre_params *p, double *cS_out)
+{
+    std::vector<int> sides;
+    std::vector<double> cexp, cS;
+    smre_status st = check_params(p, sides, cexp);
+    if (st != SMRE_OK) return st;
+    if (!cS_out) return fail(nullptr, SMRE_EINVAL, "cS_out is NULL");
+    st = compute_bounds(p, sides, cexp, cS);
+    if (st != SMRE_OK) return st;
+    for (int i = 0; i < p->n_sides; ++i) {
+        const int L = p->sides[i];
+        const size_t j = std::lower_bound(sides.begin(), sides.end(), L) - sides.begin();
+        cS_out[i] = cS[j];
+    }
+    return SMRE_OK;
+}
+
+smre_status smre_dykstra_create(const smre_params *p, void *cuda_stream, smre_dykstra **out)
+{
+    if (!out) return fail(nullptr, SMRE_EINVAL, "out is NULL");
+    *out = nullptr;
+    std::vector<int> sides;
+    std::vector<double> cexp;
+    smre_status st = check_params(p, sides, cexp);
+    if (st != SMRE_OK) return st;
+    smre_dykstra *h = new (std::nothrow) smre_dykstra();
+    if (!h) return fail(nullptr, SMRE_ENOMEM, "host allocation failed");
+    h->H = p->height;
+    h->W = p->width;
+    h->pitch = round_up(p->width, 32);
+    h->sides = sides;
+    h->cmode = p->cmode;
+    h->alpha = p->alpha;
+    h->maxstat_draws = p->maxstat_draws ? p->maxstat_draws : 1000;
+    h->seed = p->seed;
+    h->flags = p->flags;
+    h->max_ctas = p->max_ctas;
+    h->q_dtype = p->q_dtype;
+    h->max_cycles = p->max_cycles;
+    h->tol = p->tol;
+    h->tol_relative = p->tol_relative ? 1 : 0;
+    h->icd_max_sweeps = p->icd_max_sweeps ? p->icd_max_sweeps : 1000;
+    h->stream = (cudaStream_t)cuda_stream;
+
+    st = compute_bounds(p, sides, cexp, h->cS);
+    if (st != SMRE_OK) {
+        delete h;
+        return st;
+    }
+    for (size_t i = 0; i < sides.size(); ++i) h->cS_of[sides[i]] = h->cS[i];
+    build_schedule(h);
+    const bool tune = (p->flags & SMRE_F_AUTOTUNE) != 0;
+    const bool batched = use_batch(p, sides.back());
+    const bool batch_fits = p->width <= kBatchMaxWidth && sides.back() <= kBatchMaxSide;
+    if (batched && !tune) h->q_floats = 0;   // the batch holds the increments
+    if (p->q_dtype != SMRE_Q_FP32) h->q_floats = 0;
+
+    auto bail = [&](smre_status s2) {
+        g_err = h->err;
+        smre_dykstra_destroy(h);
+        return s2;
+    };
+#define CKC(call)                                                                         \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess) {                                                          \
+            fail(h, e_ == cudaErrorMemoryAllocation ? SMRE_ENOMEM : SMRE_ECUDA, "%s: %s", \
+                 #call, cudaGetErrorString(e_));                                          \
+            return bail(e_ == cudaErrorMemoryAllocation ? SMRE_ENOMEM : SMRE_ECUDA);     \
+        }                                                                                 \
+    } while (0)
+
+    const size_t img = sizeof(float) * (size_t)h->H * h->pitch;
+    CKC(cudaMalloc(&h->q, sizeof(float) * std::max<size_t>(h->q_floats, 1)));
+    CKC(cudaMalloc(&h->xw, img));
+    CKC(cudaMalloc(&h->xprev, img));
+    CKC(cudaMemset(h->xw, 0, img));
+    CKC(cudaMemset(h->xprev, 0, img));
+    h->n_partials = norm_blocks();
+    CKC(cudaMalloc(&h->partials, sizeof(double) * 2 * h->n_partials));
+    CKC(cudaMalloc(&h->ctl, sizeof(Control)));
+    CKC(cudaMalloc(&h->viol, sizeof(double)));
+    CKC(cudaMallocHost(&h->ctl_host, sizeof(Control)));
+    CKC(cudaMallocHost(&h->viol_host, sizeof(double)));
+    CKC(cudaEventCreate(&h->ev0));
+    CKC(cudaEventCreate(&h->ev1));
+    h->dev_bytes = sizeof(float) * std::max<size_t>(h->q_floats, 1) + 2 * img +
+                   sizeof(double) * 2 * h->n_partials + sizeof(Control) + sizeof(double);
+    if (ensure_hist(h, h->max_cycles) != SMRE_OK) return bail(SMRE_ENOMEM);
+    if (tune) {
+        // every schedule that can run the shape, then time them
+        if (p->q_dtype == SMRE_Q_FP32 && plan_persistent(h, p->flags) != SMRE_OK)
+            return bail(SMRE_ECUDA);
+        if (batch_fits) {
+            st = make_handle_batch(h);
+            if (st != SMRE_OK) return bail(st);
+        }
+        st = autotune(h);
+        if (st != SMRE_OK) return bail(st);
+    } else if (batched) {
+        st = make_handle_batch(h);
+        if (st != SMRE_OK) return bail(st);
+    } else if (plan_persistent(h, p->flags) != SMRE_OK) {
+        return bail(SMRE_ECUDA);
+    }
+#undef CKC
+    *out = h;
+    return SMRE_OK;
+}
+
+smre_status smre_dykstra_set_stopping(smre_dykstra *h, int max_cycles, double tol, int tol_relative)
+{
+    if (!h) return fail(nullptr, SMRE_EINVAL, "handle is NULL");
+    if (max_cycles < 1) return fail(h, SMRE_EINVAL, "max_cycles must be >= 1");
+    if (std::isnan(tol)) return fail(h, SMRE_EINVAL, "tol is NaN");
+    smre_status st = ensure_hist(h, max_cycles);
+    if (st != SMRE_OK) return st;
+    h->max_cycles = max_cycles;
+    h->tol = tol;
+    h->tol_relative = tol_relative ? 1 : 0;
+    if (h->bat && batch_set_rule(h->bat, max_cycles, tol, tol_relative) != SMRE_OK)
+        return make_handle_batch(h);   // more cycles than its history holds: a new batch
+    return SMRE_OK;
+}
+
+smre_status smre_dykstra_project(smre_dykstra *h, const float *x0, float *x, smre_result *res)
+{
+    if (!h) return fail(nullptr, SMRE_EINVAL, "handle is NULL");
+    return project_core(h, x0, x, res);
+}
+
+int smre_dykstra_schedule(const smre_dykstra *h) { return h ? current_schedule(h) : 0; }
 
 smre_status smre_dykstra_project_incomplete(smre_dykstra *h, const float *x0, float *x, int K,
                                             double tol, smre_result *res)

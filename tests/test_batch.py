@@ -288,3 +288,26 @@ def test_handle_runs_16bit_and_wide_images_through_a_batch(smre, torch_cuda, ora
             assert P.device_bytes() > 0
     with pytest.raises(smre.SmreError):
         smre.Projector(40, 2100, sides, q_dtype=smre.SMRE_Q_BF16, **kw)   # wider than 2048
+
+
+def test_autotuned_schedule_gives_the_same_answer(smre, torch_cuda, oracle_mod):
+    """SMRE_F_AUTOTUNE times the schedules that can run the shape and keeps
+    one; every schedule computes the same bits, and the choice is cached."""
+    torch = torch_cuda
+    sides = list(range(1, 7))
+    cS = oracle_mod.bounds(sides, 0.9)
+    for shape in ((300, 1000), (64, 1500)):
+        (x0,) = images([shape], seed0=701)
+        kw = dict(cmode=smre.SMRE_C_EXPLICIT, c_explicit=list(cS), max_cycles=4, tol=-1.0)
+        group = single(smre, torch, x0, sides, cS, 4, smre.SMRE_F_GROUP_LAUNCHES)
+        xd = torch.from_numpy(x0).cuda()
+        with smre.Projector(*shape, sides, flags=smre.SMRE_F_AUTOTUNE, **kw) as P:
+            sched = P.schedule()
+            assert sched in (smre.SMRE_SCHED_PERSISTENT, smre.SMRE_SCHED_BATCHED,
+                             smre.SMRE_SCHED_GROUPS)
+            out = torch.empty_like(xd)
+            r = P.project(xd, out)
+            assert r.cycles == 4
+            assert np.array_equal(out.cpu().numpy(), group)
+        with smre.Projector(*shape, sides, flags=smre.SMRE_F_AUTOTUNE, **kw) as P:
+            assert P.schedule() == sched          # cached for the shape
