@@ -116,6 +116,14 @@ struct BItem {
     int slot, u0, nu;
 };
 
+// What the consumers need of an item, published by the producer with the
+// item's x chunk (so the consumers never wait on the item tables in HBM);
+// P < 0 marks the end of the CTA's items.
+struct ChunkInfo {
+    float *xrow;   // the item's first image row (x)
+    int P, W, nu, first;
+};
+
 // 2^(k + shift) for the smallest k with v <= 2^k (exponent k in ex), read from
 // the bits of v; 0 when v is zero, subnormal, not finite, or the power would
 // leave the normal range (increments that small are stored as zero).
@@ -239,7 +247,7 @@ __device__ inline bool wait_phase(uint64_t *bar, unsigned parity, const BStepArg
 // and nothing is read.  Lane 0 keeps the ring; every lane issues copies.
 template <typename QT, int VW>
 __device__ void produce(const BStepArgs &A, unsigned char *ring, uint64_t *full,
-                        uint64_t *written, int *s_off, volatile int *s_abort)
+                        uint64_t *written, int *s_off, ChunkInfo *s_info, volatile int *s_abort)
 {
     constexpr bool MIXED = QConv<QT>::mixed;
     constexpr int esz = (int)sizeof(QT);
@@ -280,7 +288,7 @@ __device__ void produce(const BStepArgs &A, unsigned char *ring, uint64_t *full,
     };
     // a chunk of n bytes whose copies will bring tx bytes (0: nothing is
     // copied); lane 0 places it and arms its barrier, all lanes learn where
-    auto begin = [&](int n, unsigned tx, int &at, int &d) -> bool {
+    auto begin = [&](int n, unsigned tx, int &at, int &d, const ChunkInfo *info) -> bool {
         int ok = 1;
         at = 0;
         d = 0;
@@ -288,6 +296,7 @@ __device__ void produce(const BStepArgs &A, unsigned char *ring, uint64_t *full,
             ok = alloc(round128(n), at) ? 1 : 0;
             if (ok) {
                 s_off[d_next] = at;
+                if (info) s_info[d_next] = *info;   // published by the arrive below
                 if (tx) mbar_arrive_expect_tx(&full[d_next], tx);
                 else mbar_arrive(&full[d_next]);
                 fiss ^= 1u << d_next;
@@ -310,12 +319,13 @@ __device__ void produce(const BStepArgs &A, unsigned char *ring, uint64_t *full,
         const int P = im.pitch;
         const bool first = im.ctl->cycles == 0;
         const int rows = it.nu * L;   // row r = unit r / L, row r % L of it
+        float *xsrc = im.x + (size_t)(A.a + L * it.u0) * P;
+        const ChunkInfo info{xsrc, P, im.W, it.nu, first ? 1 : 0};
         int at, d;
-        if (!begin(L * VW * 4, (unsigned)(rows * P) * 4u, at, d)) {
+        if (!begin(L * VW * 4, (unsigned)(rows * P) * 4u, at, d, &info)) {
             dead = true;
             break;
         }
-        const float *xsrc = im.x + (size_t)(A.a + L * it.u0) * P;
         for (int r = lane; r < rows; r += 32) {
             const int s = r / L, i = r - s * L;
             bulk_load(ring + at + (size_t)(i * VW + s * P) * 4, xsrc + (size_t)r * P,
@@ -325,7 +335,7 @@ __device__ void produce(const BStepArgs &A, unsigned char *ring, uint64_t *full,
         const unsigned tx = first ? 0u
                                   : (unsigned)(rows * P * esz) + (MIXED ? (unsigned)(it.nu * nwp) * 4u : 0u);
         for (int b = 0; b < L; ++b) {
-            if (!begin(L * VW * esz + (MIXED ? VW * 4 : 0), tx, at, d)) {
+            if (!begin(L * VW * esz + (MIXED ? VW * 4 : 0), tx, at, d, nullptr)) {
                 dead = true;
                 break;
             }
@@ -341,6 +351,11 @@ __device__ void produce(const BStepArgs &A, unsigned char *ring, uint64_t *full,
                 bulk_load(ring + at + (size_t)L * VW * esz, im.qs + im.soff[A.p0 + b] + (size_t)it.u0 * nwp,
                           (unsigned)(it.nu * nwp) * 4u, &full[d]);
         }
+    }
+    if (!dead) {   // the end marker: a chunk without data
+        const ChunkInfo end{nullptr, -1, 0, 0, 0};
+        int at, d;
+        if (!begin(128, 0u, at, d, &end)) dead = true;
     }
     if (lane != 0) return;
     if (!dead) {
@@ -428,6 +443,7 @@ __global__ void __launch_bounds__(kThreads, 1) bstep_kernel(const BStepArgs A)
     WD *wdat = reinterpret_cast<WD *>(part64 + VW);                 // [VW]
     unsigned char *ring = smem + A.ring_offset;
     __shared__ volatile int s_abort;
+    __shared__ ChunkInfo s_info[kD];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int L = EXACT ? LB : A.L;
@@ -444,7 +460,7 @@ __global__ void __launch_bounds__(kThreads, 1) bstep_kernel(const BStepArgs A)
     __syncthreads();
 
     if (warp == kNCW) {
-        produce<QT, VW>(A, ring, full, written, s_off, &s_abort);
+        produce<QT, VW>(A, ring, full, written, s_off, s_info, &s_abort);
         return;
     }
     if (warp == kNCW + 1) {
@@ -456,12 +472,19 @@ __global__ void __launch_bounds__(kThreads, 1) bstep_kernel(const BStepArgs A)
     int dc = 0;          // descriptor of the next chunk
     unsigned fph = 0;    // parity of the next `full` wait, per descriptor
     const float cS = A.cS, sqrt_cS = A.sqrt_cS;
-    for (int item = blockIdx.x; item < A.n_items; item += gridDim.x) {
-        const BItem it = decode_item(A, item);
-        const BImage im = A.imgs[it.slot];
-        if (im.ctl->stop) continue;
-        const int P = im.pitch, W = im.W;
-        const bool first = im.ctl->cycles == 0;
+    for (;;) {
+        // the next item's x chunk, with the item's description
+        bool bad = !wait_phase(&full[dc], (fph >> dc) & 1u, A, &s_abort);
+        fph ^= 1u << dc;
+        if (named_sync_or(1, bad, kNC)) break;
+        const ChunkInfo info = s_info[dc];
+        if (info.P < 0) {   // no more items
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&written[dc]);
+            break;
+        }
+        const int P = info.P, W = info.W, nu = info.nu;
+        const bool first = info.first != 0;
         const int nwp = scale_row(W, L);
         // Thread t owns the column pairs (c, c + 1), c = 2 (t + kNC j) mod P of
         // unit sj of the item.  o: row-0 offset of the pair in a chunk; po: its
@@ -476,7 +499,7 @@ __global__ void __launch_bounds__(kThreads, 1) bstep_kernel(const BStepArgs A)
             const int c = vc - sj * P;
             og[j] = sj * L * P + c;   // row 0 of the pair in the image rows of the item
             so[j] = sj * nwp;
-            vv[j] = sj < it.nu && c < W ? c / L : kOutside;
+            vv[j] = sj < nu && c < W ? c / L : kOutside;
             rr[j] = c % L;
         }
         // this thread's first pair in a chunk row and in the column sums; pair j
@@ -485,8 +508,6 @@ __global__ void __launch_bounds__(kThreads, 1) bstep_kernel(const BStepArgs A)
 
         // the item's rows of x into registers
         float2 x[LB][CPP];   // (column c, column c + 1); pairs use the FP32x2 arithmetic
-        bool bad = !wait_phase(&full[dc], (fph >> dc) & 1u, A, &s_abort);
-        fph ^= 1u << dc;
         {
             const float *xb = reinterpret_cast<const float *>(ring + s_off[dc]) + vc0;
 #pragma unroll
@@ -663,7 +684,7 @@ __global__ void __launch_bounds__(kThreads, 1) bstep_kernel(const BStepArgs A)
         if (aborted) break;
         // the item's rows of x back to HBM (both columns of a pair; a column
         // past the width lands in the row's padding)
-        float *xg = im.x + (size_t)(A.a + L * it.u0) * P;
+        float *xg = info.xrow;
 #pragma unroll
         for (int j = 0; j < CPP; ++j)
             if (vv[j] > kOutside + kBatchMaxSide) {
