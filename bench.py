@@ -321,7 +321,7 @@ def bench_mixed(smre, torch, stream, peak, threads):
     return out
 
 
-def bench_serving(smre, torch, stream, n_req=64, rate=500.0):
+def bench_serving(smre, torch, stream, n_req=64, rate=500.0, slots=16):
     """Poisson arrivals (mean `rate` per second) of square SOFI-like requests,
     side uniform in 64..2048, window sides 1..8, BF16 increments, at most 100
     cycles or a relative step of 1e-6: the request loop against the plain
@@ -337,7 +337,7 @@ def bench_serving(smre, torch, stream, n_req=64, rate=500.0):
               tol_relative=True)
     outs = [np.empty_like(a) for a in imgs]
     with smre.Server(SIDES, cycles_per_round=4, stream=stream, q_dtype=smre.SMRE_Q_BF16,
-                     max_images=64, device_bytes=48 << 30, **kw) as S:
+                     max_images=slots, device_bytes=48 << 30, **kw) as S:
         t0 = time.perf_counter()
         tickets = []
         for a, img, o in zip(arrivals, imgs, outs):
@@ -366,7 +366,7 @@ def bench_serving(smre, torch, stream, n_req=64, rate=500.0):
     lat.sort()
     plain = {"images_per_s": n_req / t_plain, "p50_s": lat[len(lat) // 2],
              "p99_s": lat[min(len(lat) - 1, int(round(0.99 * (len(lat) - 1))))]}
-    return {"requests": n_req, "rate_per_s": rate, "sides": "1..8",
+    return {"requests": n_req, "rate_per_s": rate, "sides": "1..8", "slots": slots,
             "stop": "rel step < 1e-6 or 100 cycles", "served_bf16": served,
             "plain_single_image_fp32": plain,
             "images_per_s_ratio": served["images_per_s"] / plain["images_per_s"]}
