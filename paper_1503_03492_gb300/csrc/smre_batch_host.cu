@@ -136,6 +136,13 @@ struct smre_batch {
     std::vector<int> step_items, step_prefix_at, step_kpack_at;
     int norm_chunks = 0, norm_prefix_at = 0;
     long long launches = 0;
+    // one cycle's launches captured in a CUDA graph, rebuilt when the item
+    // tables or the stopping rule change
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    bool graph_dirty = true;
+    bool graph_ok = true;
+    int cycle_kernels = 0;
     std::string err;
 };
 
@@ -263,13 +270,19 @@ smre_status rebuild_tables(smre_batch *b)
         const Step &st = b->steps[s];
         const int vw = batch_virtual_width(st.L);
         b->step_prefix_at[s] = (int)tab.size();
+        // units per item: as many as fit the kernel's width (a pass's fixed
+        // costs are paid per item), but few enough that the step's items
+        // cover every SM (few or small images)
+        long long total_units = 0;
+        for (int i = 0; i < n; ++i) total_units += (b->slots[b->active[i]].H - st.a) / st.L;
+        const int kcap = (int)std::max(1LL, (total_units + b->sms - 1) / b->sms);
         int acc = 0;
         std::vector<int> kp(n);
         for (int i = 0; i < n; ++i) {
             const auto &sl = b->slots[b->active[i]];
             tab.push_back(acc);
             const int units = (sl.H - st.a) / st.L;
-            const int k = std::max(1, vw / sl.img.pitch);
+            const int k = std::max(1, std::min(vw / sl.img.pitch, kcap));
             kp[i] = k;
             acc += (units + k - 1) / k;
         }
@@ -290,13 +303,85 @@ smre_status rebuild_tables(smre_batch *b)
     BCK(b, cudaMemcpyAsync(b->d_tab, tab.data(), sizeof(int) * tab.size(), cudaMemcpyHostToDevice,
                            b->stream));
     b->dirty = false;
+    b->graph_dirty = true;
     return SMRE_OK;
+}
+
+// The launches of one cycle: one step kernel per group with items, then the
+// norm and the stopping test.
+smre_status enqueue_cycle(smre_batch *b, cudaStream_t stream)
+{
+    const int n = (int)b->active.size();
+    int kernels = 0;
+    for (size_t s = 0; s < b->steps.size(); ++s) {
+        if (b->step_items[s] == 0) continue;
+        const Step &st = b->steps[s];
+        BStepArgs A{};
+        A.imgs = b->d_imgs;
+        A.active = b->d_tab;
+        A.prefix = b->d_tab + b->step_prefix_at[s];
+        A.kpack = b->d_tab + b->step_kpack_at[s];
+        A.n_active = n;
+        A.n_items = b->step_items[s];
+        A.L = st.L;
+        A.a = st.a;
+        A.p0 = st.p0;
+        A.cS = (float)b->cS_of[st.L];
+        A.sqrt_cS = (float)std::sqrt(b->cS_of[st.L]);
+        A.cS64 = b->cS_of[st.L];
+        A.ring_offset = (int)(256 + batch_part_bytes(st.L, b->qtype));
+        A.ring_bytes = (int)(b->smem - A.ring_offset);
+        A.timeout_ns = b->timeout_ns;
+        A.err = b->d_err;
+        const int grid = std::min(A.n_items, b->sms);
+        BCK(b, launch_batch_step(b->qtype, A, grid, b->smem, stream));
+        ++kernels;
+    }
+    BNormArgs N{b->d_imgs, b->d_tab, b->d_tab + b->norm_prefix_at, n, b->norm_chunks};
+    BCK(b, launch_batch_norm(N, std::min(b->norm_chunks, 4 * b->sms), stream));
+    BDecideArgs D{b->d_imgs, b->d_tab, n, b->max_cycles, b->tol, b->tol_relative};
+    BCK(b, launch_batch_decide(D, stream));
+    kernels += 2;
+    b->cycle_kernels = kernels;
+    b->launches += kernels;
+    return SMRE_OK;
+}
+
+// Capture one cycle into a graph on the batch's private stream (launched
+// later on the caller's stream).  If capture is not possible the batch keeps
+// launching the kernels one by one.
+void capture_cycle(smre_batch *b)
+{
+    if (b->gexec) {
+        cudaGraphExecDestroy(b->gexec);
+        b->gexec = nullptr;
+    }
+    b->graph_dirty = false;
+    const long long l0 = b->launches;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        b->graph_ok = false;
+        return;
+    }
+    const smre_status st = enqueue_cycle(b, b->cap_stream);
+    const cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
+    b->launches = l0;   // captured, not launched
+    if (st != SMRE_OK || e != cudaSuccess || !g ||
+        cudaGraphInstantiate(&b->gexec, g, 0) != cudaSuccess) {
+        cudaGetLastError();
+        b->gexec = nullptr;
+        b->graph_ok = false;
+    }
+    if (g) cudaGraphDestroy(g);
 }
 
 void free_batch(smre_batch *b)
 {
     if (!b) return;
     if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     cudaFree(b->arena);
     cudaFree(b->d_imgs);
     cudaFree(b->d_ctl);
@@ -398,6 +483,7 @@ smre_status smre_batch_create(const smre_batch_params *p, void *cuda_stream, smr
     CREATE_CK(cudaMalloc(&b->d_tab, sizeof(int) * b->tab_ints));
     CREATE_CK(cudaMallocHost(&b->h_ctl, sizeof(Control) * b->max_images));
     CREATE_CK(cudaMallocHost(&b->h_err, sizeof(int)));
+    CREATE_CK(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
     memset(b->h_ctl, 0, sizeof(Control) * b->max_images);
     *b->h_err = 0;
 #undef CREATE_CK
@@ -493,37 +579,15 @@ smre_status smre_batch_run(smre_batch *b, int cycles)
         smre_status st = rebuild_tables(b);
         if (st != SMRE_OK) return st;
     }
-    const int n = (int)b->active.size();
+    if (b->graph_ok && b->graph_dirty) capture_cycle(b);
     for (int c = 0; c < cycles; ++c) {
-        for (size_t s = 0; s < b->steps.size(); ++s) {
-            if (b->step_items[s] == 0) continue;
-            const Step &st = b->steps[s];
-            BStepArgs A{};
-            A.imgs = b->d_imgs;
-            A.active = b->d_tab;
-            A.prefix = b->d_tab + b->step_prefix_at[s];
-            A.kpack = b->d_tab + b->step_kpack_at[s];
-            A.n_active = n;
-            A.n_items = b->step_items[s];
-            A.L = st.L;
-            A.a = st.a;
-            A.p0 = st.p0;
-            A.cS = (float)b->cS_of[st.L];
-            A.sqrt_cS = (float)std::sqrt(b->cS_of[st.L]);
-            A.cS64 = b->cS_of[st.L];
-            A.ring_offset = (int)(256 + batch_part_bytes(st.L, b->qtype));
-            A.ring_bytes = (int)(b->smem - A.ring_offset);
-            A.timeout_ns = b->timeout_ns;
-            A.err = b->d_err;
-            const int grid = std::min(A.n_items, b->sms);
-            BCK(b, launch_batch_step(b->qtype, A, grid, b->smem, b->stream));
-            ++b->launches;
+        if (b->gexec) {
+            BCK(b, cudaGraphLaunch(b->gexec, b->stream));
+            b->launches += b->cycle_kernels;
+        } else {
+            smre_status st = enqueue_cycle(b, b->stream);
+            if (st != SMRE_OK) return st;
         }
-        BNormArgs N{b->d_imgs, b->d_tab, b->d_tab + b->norm_prefix_at, n, b->norm_chunks};
-        BCK(b, launch_batch_norm(N, std::min(b->norm_chunks, 4 * b->sms), b->stream));
-        BDecideArgs D{b->d_imgs, b->d_tab, n, b->max_cycles, b->tol, b->tol_relative};
-        BCK(b, launch_batch_decide(D, b->stream));
-        b->launches += 2;
     }
     return SMRE_OK;
 }
@@ -686,6 +750,7 @@ smre_status batch_set_rule(smre_batch *b, int max_cycles, double tol, int tol_re
     b->max_cycles = max_cycles;
     b->tol = tol;
     b->tol_relative = tol_relative ? 1 : 0;
+    b->graph_dirty = true;
     return SMRE_OK;
 }
 
