@@ -656,7 +656,7 @@ smre_status plan_persistent(smre_dykstra *h, int flags)
     if (S < 3) return SMRE_OK;
     const size_t smem = stage_offset + (size_t)S * stage_floats * 4 + xs_bytes;
     int occ = 0;
-    cudaError_t oe = persist_occupancy(sp, threads, smem, &occ);
+    cudaError_t oe = persist_occupancy(sp, pitch, threads, smem, &occ);
     if (oe != cudaSuccess || occ < 1) {
         cudaGetLastError();
         return SMRE_OK;
@@ -834,7 +834,7 @@ void set_thread_error(const char *msg) { g_err = msg; }
 
 extern "C" {
 
-const char *smre_version(void) { return "smre-gb300 0.3 (sm_103a)"; }
+const char *smre_version(void) { return "smre-gb300 0.4 (sm_103a)"; }
 
 const char *smre_last_error(const smre_dykstra *h)
 {

@@ -207,7 +207,7 @@ smre_status batch_retrieve_ld(smre_batch *b, int slot, float *x, int ld, smre_re
 bool persist_supported(int max_side);
 // shared-memory row stride (power of two >= pitch, 128..1024) or 0 if too wide
 int persist_smem_pitch(int pitch);
-cudaError_t persist_occupancy(int sp, int threads, size_t smem, int *blocks_per_sm);
+cudaError_t persist_occupancy(int sp, int pitch, int threads, size_t smem, int *blocks_per_sm);
 cudaError_t launch_persist(const PersistArgs &A, int sp, int grid, int threads, size_t smem,
                            cudaStream_t s);
 

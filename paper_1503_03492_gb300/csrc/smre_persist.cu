@@ -128,15 +128,17 @@ struct PassCtx {
 
 // The L passes b = 0..L-1 of one task, side L known at compile time.  Returns
 // true when the launch must be abandoned (a copy did not arrive in time).
-template <int L, int SP>
+template <int L, int SP, bool PEQ>
 __device__ __forceinline__ bool run_passes(const PassCtx &cx, const PassTask &ts, int &s_cur,
                                            unsigned &fph)
 {
     // SP: row stride of x and of the stages in shared memory (compile time,
-    // so every shared-memory access of a pass uses an immediate offset)
+    // so every shared-memory access of a pass uses an immediate offset);
+    // PEQ: the image pitch equals SP, so the increment stores in HBM use
+    // immediate row offsets too
     constexpr int wpw = 32 / L;                     // windows per warp
     constexpr int MI = max_items_for_side(L);       // items per warp and task
-    const int lane = cx.lane, warp = cx.warp, pitch = cx.pitch;
+    const int lane = cx.lane, warp = cx.warp, pitch = PEQ ? SP : cx.pitch;
     const int wl = lane / L, col = lane - wl * L;   // window of the lane, column in it
     const int base = wl * L;
     const bool lane_on = lane < wpw * L;
@@ -192,7 +194,13 @@ __device__ __forceinline__ bool run_passes(const PassCtx &cx, const PassTask &ts
             float sq = 0.f;
             if (on) {
 #pragma unroll
-                for (int i = 0; i < L; ++i) y[i] = xr[i * SP] + qr[i * SP];
+                for (int i = 0; i + 1 < L; i += 2) {   // FP32x2: rows i, i + 1
+                    const float2 s2 = __fadd2_rn(make_float2(xr[i * SP], xr[(i + 1) * SP]),
+                                                 make_float2(qr[i * SP], qr[(i + 1) * SP]));
+                    y[i] = s2.x;
+                    y[i + 1] = s2.y;
+                }
+                if (L & 1) y[L - 1] = xr[(L - 1) * SP] + qr[(L - 1) * SP];
 #pragma unroll
                 for (int i = 0; i < L; ++i) sq = fmaf(y[i], y[i], sq);
             }
@@ -216,11 +224,23 @@ __device__ __forceinline__ bool run_passes(const PassCtx &cx, const PassTask &ts
                 if (near) scale = t64 > ts.cS64 ? (float)sqrt(ts.cS64 / t64) : 1.f;
             }
             if (on) {
+                // x = y * scale, q = y - x (FP32x2 on row pairs; streaming stores:
+                // the increments are read again only next cycle)
+                const float2 sc2 = make_float2(scale, scale);
 #pragma unroll
-                for (int i = 0; i < L; ++i) {
-                    const float xn = y[i] * scale;
-                    xr[i * SP] = xn;
-                    __stcs(qw + i * pitch, y[i] - xn);   // streaming store: read again next cycle
+                for (int i = 0; i + 1 < L; i += 2) {
+                    const float2 y2 = make_float2(y[i], y[i + 1]);
+                    const float2 n2 = __fmul2_rn(y2, sc2);
+                    const float2 q2 = __fadd2_rn(y2, make_float2(-n2.x, -n2.y));
+                    xr[i * SP] = n2.x;
+                    xr[(i + 1) * SP] = n2.y;
+                    __stcs(qw + i * pitch, q2.x);
+                    __stcs(qw + (i + 1) * pitch, q2.y);
+                }
+                if (L & 1) {
+                    const float xn = y[L - 1] * scale;
+                    xr[(L - 1) * SP] = xn;
+                    __stcs(qw + (L - 1) * pitch, y[L - 1] - xn);
                 }
             }
         }
@@ -234,12 +254,12 @@ __device__ __forceinline__ bool run_passes(const PassCtx &cx, const PassTask &ts
     return false;
 }
 
-template <int SP>
+template <int SP, bool PEQ>
 __device__ __forceinline__ bool run_task_passes(const PassCtx &cx, const PassTask &ts, int &s_cur,
                                                 unsigned &fph)
 {
     switch (ts.L) {
-#define RP(l) case l: return run_passes<l, SP>(cx, ts, s_cur, fph);
+#define RP(l) case l: return run_passes<l, SP, PEQ>(cx, ts, s_cur, fph);
         RP(1) RP(2) RP(3) RP(4) RP(5) RP(6) RP(7) RP(8)
         RP(9) RP(10) RP(11) RP(12) RP(13) RP(14) RP(15) RP(16)
 #undef RP
@@ -330,7 +350,7 @@ enum { kGo = 0, kStop = 1, kAbort = 2 };
 // k * wpw + l / L of its warp's chunk k; a window's column sums meet by
 // shuffles in a fixed order, so every lane of a window sees the same sum.
 // x of the task's rows lives in shared memory for the task's L passes.
-template <int SP>
+template <int SP, bool PEQ>
 __global__ void __launch_bounds__(kPersistThreads, 1) persist_kernel(const PersistArgs A)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -519,7 +539,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1) persist_kernel(const Persi
                 }
                 if (gp.U > 0) {
                     const PassTask pt{L, gp.U, sd.pass0 + a * L, sd.cS, sd.sqrt_cS, sd.cS64};
-                    const bool ab = run_task_passes<SP>(cx, pt, s_cur, fph);
+                    const bool ab = run_task_passes<SP, PEQ>(cx, pt, s_cur, fph);
                     if (consumers_sync_or(ab, NC)) { aborted = true; break; }
                 }
                 // publish: the top row (dropped next), or the whole band at the end
@@ -621,24 +641,24 @@ __global__ void __launch_bounds__(kPersistThreads, 1) persist_kernel(const Persi
     }
 }
 
-template <int SP>
+template <int SP, bool PEQ>
 cudaError_t launch_persist_t(const PersistArgs &A, int grid, int threads, size_t smem,
                              cudaStream_t s)
 {
-    auto k = persist_kernel<SP>;
+    auto k = persist_kernel<SP, PEQ>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     void *args[] = {const_cast<PersistArgs *>(&A)};
     return cudaLaunchCooperativeKernel((const void *)k, dim3(grid), dim3(threads), args, smem, s);
 }
 
-const void *kernel_for(int sp)
+const void *kernel_for(int sp, bool peq)
 {
     switch (sp) {
-        case 128: return (const void *)persist_kernel<128>;
-        case 256: return (const void *)persist_kernel<256>;
-        case 512: return (const void *)persist_kernel<512>;
-        case 1024: return (const void *)persist_kernel<1024>;
+        case 128: return peq ? (const void *)persist_kernel<128, true> : (const void *)persist_kernel<128, false>;
+        case 256: return peq ? (const void *)persist_kernel<256, true> : (const void *)persist_kernel<256, false>;
+        case 512: return peq ? (const void *)persist_kernel<512, true> : (const void *)persist_kernel<512, false>;
+        case 1024: return peq ? (const void *)persist_kernel<1024, true> : (const void *)persist_kernel<1024, false>;
         default: return nullptr;
     }
 }
@@ -654,9 +674,9 @@ int persist_smem_pitch(int pitch)
 
 bool persist_supported(int max_side) { return max_side >= 1 && max_side <= 16; }
 
-cudaError_t persist_occupancy(int sp, int threads, size_t smem, int *blocks_per_sm)
+cudaError_t persist_occupancy(int sp, int pitch, int threads, size_t smem, int *blocks_per_sm)
 {
-    const void *k = kernel_for(sp);
+    const void *k = kernel_for(sp, pitch == sp);
     if (!k) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -666,11 +686,16 @@ cudaError_t persist_occupancy(int sp, int threads, size_t smem, int *blocks_per_
 cudaError_t launch_persist(const PersistArgs &A, int sp, int grid, int threads, size_t smem,
                            cudaStream_t s)
 {
+    const bool peq = A.pitch == sp;
     switch (sp) {
-        case 128: return launch_persist_t<128>(A, grid, threads, smem, s);
-        case 256: return launch_persist_t<256>(A, grid, threads, smem, s);
-        case 512: return launch_persist_t<512>(A, grid, threads, smem, s);
-        case 1024: return launch_persist_t<1024>(A, grid, threads, smem, s);
+        case 128: return peq ? launch_persist_t<128, true>(A, grid, threads, smem, s)
+                             : launch_persist_t<128, false>(A, grid, threads, smem, s);
+        case 256: return peq ? launch_persist_t<256, true>(A, grid, threads, smem, s)
+                             : launch_persist_t<256, false>(A, grid, threads, smem, s);
+        case 512: return peq ? launch_persist_t<512, true>(A, grid, threads, smem, s)
+                             : launch_persist_t<512, false>(A, grid, threads, smem, s);
+        case 1024: return peq ? launch_persist_t<1024, true>(A, grid, threads, smem, s)
+                              : launch_persist_t<1024, false>(A, grid, threads, smem, s);
         default: return cudaErrorInvalidValue;
     }
 }
