@@ -3,23 +3,29 @@
 // One launch runs the whole projection (Sec. 2.3, Algorithm 2): every cycle
 // visits the groups (L, a) in the set order (sides descending, a ascending);
 // inside a group the L tilings (L, a, b), b = 0..L-1, only move windows
-// sideways, so a CTA that owns a band of window-rows ("units") of the group
-// runs all L passes on it with block barriers alone.  Ownership follows
-// fixed home bands of image rows, so consecutive groups of a CTA overlap and
-// most ordering is program order; a task (group, CTA) waits only for the
-// flags of the other CTAs' tasks that last touched its rows.  One grid barrier
-// per cycle gathers the FP64 norms of the stopping test.
+// sideways, so a CTA that holds a band of window-rows ("units") of the group
+// runs all L passes on it with block barriers alone.
+//
+// Side-resident bands: for each side L a CTA owns units [u0, u1) for all
+// offsets a.  Its band of x rows (rows a + L u0 .. a + L u1 - 1) stays in
+// shared memory for the whole side; from offset a to a + 1 the band slides
+// down one row: the top row is published (stored to HBM, then a release flag)
+// and the lower neighbour's published top row is taken in at the bottom
+// (acquire).  At a side change the band is stored and the next side's band
+// loaded after the flags of the CTAs that last wrote those rows.  One grid
+// barrier per cycle gathers the FP64 norms of the stopping test.
 //
 // Data movement:
 //  - increments q_s (the HBM stream, sum_L L^2 H W floats) come in through a
 //    ring of shared-memory stages filled by bulk async copies (TMA engine)
-//    that a producer warp keeps S passes ahead of the consumers; the
+//    that a producer warp keeps up to 16 passes ahead of the consumers; the
 //    consumers write the updated increments straight back to HBM with
-//    coalesced streaming stores;
-//  - x of the CTA's rows sits in registers for the L passes of a task; it goes
-//    through L2 only at task boundaries;
-//  - the cycle norm |x - x_prev|^2, |x_prev|^2 (FP64) is fused into the task
-//    that last touches each row in a cycle.
+//    streaming stores (immediate row offsets when the pitch equals the
+//    shared-memory row stride);
+//  - x lives in shared memory, in the bands; it goes through L2 only as the
+//    published rows;
+//  - the cycle norm |x - x_prev|^2, |x_prev|^2 (FP64) is fused into the
+//    publication that makes each row final in a cycle.
 //
 // Every wait (dependency flags, grid barrier, copy completion) has a time
 // limit; on expiry the kernel records SMRE_ETIMEOUT, lets its copies in
