@@ -569,32 +569,36 @@ __global__ void __launch_bounds__(kThreads, 1) bstep_kernel(const BStepArgs A)
                 break;
             }
 
-            // one thread per window (its first column) sums the L column sums in
-            // column order, takes the ball test of Eq. (dykstra:if) and, for
-            // 16-bit increments, picks the window's power-of-two scale sw with
-            // |q_i| / sw <= 2^15 (FP16 holds up to 65504) from
-            // |q_i| <= |q_s|_2 = (1 - scale) sqrt(t); windows within the band
-            // of the test are flagged for the FP64 recheck
+            // the consumers share out the pass's windows (nu rows of nv windows):
+            // for each, sum the L column sums in column order, take the ball test
+            // of Eq. (dykstra:if) and, for 16-bit increments, pick the window's
+            // power-of-two scale sw with |q_i| / sw <= 2^15 (FP16 holds up to
+            // 65504) from |q_i| <= |q_s|_2 = (1 - scale) sqrt(t); the factors go
+            // to the window's first column, windows within the band of the test
+            // are flagged for the FP64 recheck
+            const int nwin = nu * nv;
+            auto window_col = [&](int w) {   // virtual column of window w's first column
+                const int s = nu == 1 ? 0 : w / nv;
+                return s * P + b + (w - s * nv) * L;
+            };
+            auto window_sum = [&](int c0) {
+                const float *pp = part + c0;
+                float pv[LB];
+#pragma unroll
+                for (int m = 0; m < LB; ++m) pv[m] = m < L ? pp[m] : 0.f;
+                float ts = 0.f;
+#pragma unroll
+                for (int m = 0; m < LB; ++m)
+                    if (m < L) ts += pv[m];
+                return ts;
+            };
             bool near = false;
-            float tl[CPP][2];   // window sums held by their leaders
-#pragma unroll
-            for (int j = 0; j < CPP; ++j)
-#pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    tl[j][e] = 0.f;
-                    if (!on[j][e] || (e ? r1[j] : rr[j]) != 0) continue;
-                    const float *pp = part + vc0 + 2 * kNC * j + e;
-                    float pv[LB];
-#pragma unroll
-                    for (int m = 0; m < LB; ++m) pv[m] = m < L ? pp[m] : 0.f;
-                    float ts = 0.f;
-#pragma unroll
-                    for (int m = 0; m < LB; ++m)
-                        if (m < L) ts += pv[m];
-                    tl[j][e] = ts;
-                    if (fabsf(ts - cS) <= kNearBand * cS) near = true;
-                    wdat[vc0 + 2 * kNC * j + e] = window_factors<MIXED>(ts, cS, sqrt_cS, 0.0, 0.0, false);
-                }
+            for (int w = tid; w < nwin; w += kNC) {
+                const int c0 = window_col(w);
+                const float ts = window_sum(c0);
+                if (fabsf(ts - cS) <= kNearBand * cS) near = true;
+                wdat[c0] = window_factors<MIXED>(ts, cS, sqrt_cS, 0.0, 0.0, false);
+            }
             if (named_sync_or(1, near, kNC)) {
                 // rare: windows within the band get their sums again in FP64
 #pragma unroll
@@ -613,17 +617,13 @@ __global__ void __launch_bounds__(kThreads, 1) bstep_kernel(const BStepArgs A)
                         }
                     }
                 named_sync(1, kNC);
-#pragma unroll
-                for (int j = 0; j < CPP; ++j)
-#pragma unroll
-                    for (int e = 0; e < 2; ++e) {
-                        if (!on[j][e] || (e ? r1[j] : rr[j]) != 0) continue;
-                        if (fabsf(tl[j][e] - cS) > kNearBand * cS) continue;
-                        double t64 = 0.0;
-                        for (int m = 0; m < L; ++m) t64 += part64[vc0 + 2 * kNC * j + e + m];
-                        wdat[vc0 + 2 * kNC * j + e] = window_factors<MIXED>((float)t64, cS, sqrt_cS, t64, A.cS64,
-                                                                true);
-                    }
+                for (int w = tid; w < nwin; w += kNC) {
+                    const int c0 = window_col(w);
+                    if (fabsf(window_sum(c0) - cS) > kNearBand * cS) continue;
+                    double t64 = 0.0;
+                    for (int m = 0; m < L; ++m) t64 += part64[c0 + m];
+                    wdat[c0] = window_factors<MIXED>((float)t64, cS, sqrt_cS, t64, A.cS64, true);
+                }
                 named_sync(1, kNC);
             }
             // every owned column takes its window's factors
