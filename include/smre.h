@@ -367,6 +367,76 @@ SMRE_API smre_status smre_server_stats(smre_server *s, smre_server_counters *st)
 /* Finish every submitted request, stop the loop, free everything. */
 SMRE_API void smre_server_destroy(smre_server *s);
 
+/* ---- ADMM outer loop: the full estimator (Sec. 2.2, Algorithm 1) ------------
+ *
+ * Solves the split form (Eq. 3) of the multi-resolution estimator (Eq. 1)
+ *     min G(eps) + R(z)  s.t.  I = A x + eps,  z = x,
+ * G the indicator of the handle's multi-resolution set (Eq. geq), R the
+ * anisotropic total variation (Sec. 2: sum of |forward differences| along both
+ * axes, zero across the last row / column), A the convolution with a
+ * normalised Gaussian point-spread function (weights exp(-k^2 / (2 sigma^2)),
+ * |k| <= radius, per axis; zero outside the image; A is its own adjoint).
+ * Multipliers Y1 (I = A x + eps) and Y2 (z = x), penalties rho1, rho2 (Eq. 2).
+ * Start x = z = eps = Y1 = Y2 = 0; one iteration:
+ *   x   <- x - (1/gamma) [ -A(rho1 (I - A x - eps) + Y1) + rho2 (x - z) + Y2 ]
+ *          (the linearised x-step, gamma >= rho1 + rho2)
+ *   eps <- P_G(I - A x + Y1 / rho1)      (the projection of this library, from
+ *          q = 0, with the cycle cap / tolerance of the smre_params)
+ *   z   <- prox_{R / rho2}(x + Y2 / rho2) by tv_iters steps of projected
+ *          gradient on the dual, p <- clip(p + (rho2/8) D(f - D^T p / rho2), -1, 1),
+ *          z = f - D^T p / rho2, p kept from one iteration to the next
+ *   Y1  <- Y1 + rho1 (I - A x - eps),  Y2 <- Y2 + rho2 (x - z)
+ * until |x_r - x_{r-1}|_2 <= delta and |I - A x_r - eps_r|_2 <= delta (both),
+ * or max_iters iterations.  All images are H x W row-major FP32 in device
+ * memory; x, z, eps and the multipliers are FP32, the two norms FP64. */
+typedef struct {
+    double sigma;               /* std of the Gaussian PSF in pixels, > 0          */
+    int radius;                 /* PSF radius, 1..16; <= 0: ceil(3 sigma)          */
+    double rho1, rho2;          /* penalties, > 0                                  */
+    double gamma;               /* x-step 1/gamma; <= 0: 1.01 (rho1 + rho2)        */
+    int tv_iters;               /* dual steps of the TV prox per iteration, >= 0   */
+    int max_iters;              /* iteration cap, >= 1                             */
+    double delta;               /* stopping tolerance; < 0: exactly max_iters      */
+} smre_admm_params;
+
+typedef struct {
+    int iters;                  /* iterations run                                  */
+    int status;                 /* OK, or ENOTCONVERGED (delta >= 0, cap reached)  */
+    double dx;                  /* |x_r - x_{r-1}|_2 of the last iteration         */
+    double residual;            /* |I - A x_r - eps_r|_2 of the last iteration     */
+    long long dykstra_cycles;   /* cycles of all eps-steps together                */
+    double seconds;             /* wall time of the solve (host clock, synchronised) */
+    double projection_seconds;  /* device time of the eps-steps alone             */
+} smre_admm_result;
+
+typedef struct smre_admm smre_admm;
+
+/* An ADMM solver for H x W images: a projection handle made from `proj`
+ * (smre_dykstra_create; its stream is `cuda_stream`) plus the solver's
+ * images.  Errors: EINVAL, ENOMEM, ECUDA (message: smre_admm_last_error(NULL)). */
+SMRE_API smre_status smre_admm_create(const smre_params *proj, const smre_admm_params *ap,
+                                      void *cuda_stream, smre_admm **out);
+
+/* Run the loop on the observed image I (device, H x W).  x (required), z and
+ * eps (NULL: not returned) receive the final iterates (device, H x W).
+ * Returns OK, ENOTCONVERGED, EINVAL, ETIMEOUT or ECUDA. */
+SMRE_API smre_status smre_admm_solve(smre_admm *a, const float *I, float *x, float *z, float *eps,
+                                     smre_admm_result *res);
+
+/* Kernel launches of the solver's own kernels so far (the eps-steps' launches
+ * are counted by the projection handle: smre_dykstra_kernel_launches). */
+SMRE_API long long smre_admm_kernel_launches(const smre_admm *a);
+
+/* The projection handle of the eps-step (owned by a). */
+SMRE_API smre_dykstra *smre_admm_projector(smre_admm *a);
+
+/* Release everything (NULL is allowed); waits for the stream first. */
+SMRE_API void smre_admm_destroy(smre_admm *a);
+
+/* Message of the last failure on a, or of the last failed create on this
+ * thread when a is NULL.  Never NULL. */
+SMRE_API const char *smre_admm_last_error(const smre_admm *a);
+
 /* Bytes of device memory the handle holds. */
 SMRE_API size_t smre_dykstra_device_bytes(const smre_dykstra *h);
 

@@ -33,7 +33,9 @@ __all__ = [
     "smre_batch_kernel_launches", "smre_batch_device_bytes", "smre_batch_last_error",
     "smre_batch_destroy", "Batch", "smre_server_params", "smre_server_counters",
     "smre_server_create", "smre_server_submit", "smre_server_wait", "smre_server_stats",
-    "smre_server_destroy", "Server",
+    "smre_server_destroy", "Server", "smre_admm_params", "smre_admm_result", "make_admm_params",
+    "smre_admm_create", "smre_admm_solve", "smre_admm_kernel_launches", "smre_admm_projector",
+    "smre_admm_destroy", "smre_admm_last_error", "Admm",
 ]
 
 SMRE_OK, SMRE_EINVAL, SMRE_ENOMEM, SMRE_ECUDA, SMRE_ETIMEOUT, SMRE_ENOTCONVERGED = range(6)
@@ -59,7 +61,8 @@ EXPORTED = (
     "smre_batch_project", "smre_batch_active", "smre_batch_kernel_launches",
     "smre_batch_device_bytes", "smre_batch_last_error", "smre_batch_destroy",
     "smre_server_create", "smre_server_submit", "smre_server_wait", "smre_server_stats",
-    "smre_server_destroy",
+    "smre_server_destroy", "smre_admm_create", "smre_admm_solve", "smre_admm_kernel_launches",
+    "smre_admm_projector", "smre_admm_destroy", "smre_admm_last_error",
 )
 
 
@@ -105,6 +108,21 @@ class smre_server_counters(ctypes.Structure):
         ("p50_s", ctypes.c_double), ("p99_s", ctypes.c_double), ("max_s", ctypes.c_double),
         ("mean_s", ctypes.c_double), ("images_per_s", ctypes.c_double),
     ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class smre_admm_params(ctypes.Structure):
+    _fields_ = [("sigma", ctypes.c_double), ("radius", ctypes.c_int), ("rho1", ctypes.c_double),
+                ("rho2", ctypes.c_double), ("gamma", ctypes.c_double), ("tv_iters", ctypes.c_int),
+                ("max_iters", ctypes.c_int), ("delta", ctypes.c_double)]
+
+
+class smre_admm_result(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("status", ctypes.c_int), ("dx", ctypes.c_double),
+                ("residual", ctypes.c_double), ("dykstra_cycles", ctypes.c_longlong),
+                ("seconds", ctypes.c_double), ("projection_seconds", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -181,6 +199,13 @@ def load():
         "smre_server_wait": (st, [H, ctypes.c_longlong, ctypes.c_double, P(smre_result)]),
         "smre_server_stats": (st, [H, P(smre_server_counters)]),
         "smre_server_destroy": (None, [H]),
+        "smre_admm_create": (st, [P(smre_params), P(smre_admm_params), ctypes.c_void_p, P(H)]),
+        "smre_admm_solve": (st, [H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                 P(smre_admm_result)]),
+        "smre_admm_kernel_launches": (ctypes.c_longlong, [H]),
+        "smre_admm_projector": (H, [H]),
+        "smre_admm_destroy": (None, [H]),
+        "smre_admm_last_error": (ctypes.c_char_p, [H]),
         "smre_last_error": (ctypes.c_char_p, [H]),
         "smre_version": (ctypes.c_char_p, []),
     }
@@ -633,6 +658,102 @@ class Server:
             smre_server_destroy(self.s)
             self.s = None
             self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# --------------------------------------------------------------------- ADMM
+
+def make_admm_params(sigma, radius=0, rho1=1.0, rho2=1.0, gamma=0.0, tv_iters=20, max_iters=100,
+                     delta=-1.0) -> smre_admm_params:
+    p = smre_admm_params()
+    p.sigma, p.radius = float(sigma), int(radius)
+    p.rho1, p.rho2, p.gamma = float(rho1), float(rho2), float(gamma)
+    p.tv_iters, p.max_iters, p.delta = int(tv_iters), int(max_iters), float(delta)
+    return p
+
+
+def smre_admm_last_error(a=None) -> str:
+    m = load().smre_admm_last_error(a)
+    return m.decode() if m else ""
+
+
+def _acheck(status, a=None, ok=(SMRE_OK,)):
+    if status not in ok:
+        raise SmreError(status, smre_admm_last_error(a))
+    return status
+
+
+def smre_admm_create(proj: smre_params, ap: smre_admm_params, stream=None):
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    a = ctypes.c_void_p()
+    _acheck(load().smre_admm_create(ctypes.byref(proj), ctypes.byref(ap), ctypes.c_void_p(stream or 0),
+                                    ctypes.byref(a)))
+    return a.value
+
+
+def smre_admm_solve(a, I, x, z=None, eps=None):
+    """ADMM on the observed image I (device, H x W); the final x (and z, eps when
+    given) land in the caller's device images.  Returns an smre_admm_result."""
+    pI, kI = _ptr(I)
+    px, kx = _ptr(x)
+    pz, kz = _ptr(z) if z is not None else (None, None)
+    pe, ke = _ptr(eps) if eps is not None else (None, None)
+    res = smre_admm_result()
+    st = load().smre_admm_solve(a, pI, px, pz, pe, ctypes.byref(res))
+    _acheck(st, a, ok=(SMRE_OK, SMRE_ENOTCONVERGED))
+    return res
+
+
+def smre_admm_kernel_launches(a) -> int:
+    return load().smre_admm_kernel_launches(a)
+
+
+def smre_admm_projector(a):
+    return load().smre_admm_projector(a)
+
+
+def smre_admm_destroy(a):
+    load().smre_admm_destroy(a)
+
+
+class Admm:
+    """The full estimator: ``with Admm(H, W, sides, sigma=2.0, ...) as A: A.solve(I, x)``.
+    Keywords of ``make_params`` set the eps-step's projection (cycle cap,
+    tolerance, bounds); those of ``make_admm_params`` the outer loop."""
+
+    _AKEYS = ("radius", "rho1", "rho2", "gamma", "tv_iters", "max_iters", "delta")
+
+    def __init__(self, H, W, sides, sigma, stream=None, **kw):
+        akw = {k: kw.pop(k) for k in list(kw) if k in self._AKEYS}
+        self.params = make_params(H, W, sides, **kw)
+        self.aparams = make_admm_params(sigma, **akw)
+        self.a = smre_admm_create(self.params, self.aparams, stream)
+
+    def solve(self, I, x, z=None, eps=None):
+        return smre_admm_solve(self.a, I, x, z, eps)
+
+    def kernel_launches(self):
+        return smre_admm_kernel_launches(self.a)
+
+    def projection_launches(self):
+        return smre_dykstra_kernel_launches(smre_admm_projector(self.a))
+
+    def close(self):
+        if self.a:
+            smre_admm_destroy(self.a)
+            self.a = None
 
     def __enter__(self):
         return self

@@ -40,7 +40,7 @@ def sources():
 
 
 def _deps():
-    return sources() + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")] + \
+    return sources() + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))] + \
         [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)]
 
 

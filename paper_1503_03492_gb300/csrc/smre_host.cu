@@ -834,7 +834,7 @@ void set_thread_error(const char *msg) { g_err = msg; }
 
 extern "C" {
 
-const char *smre_version(void) { return "smre-gb300 0.4 (sm_103a)"; }
+const char *smre_version(void) { return "smre-gb300 0.5 (sm_103a)"; }
 
 const char *smre_last_error(const smre_dykstra *h)
 {

@@ -95,3 +95,14 @@ def test_product_package_does_not_reach_the_oracle():
                 txt = open(os.path.join(dirpath, fn)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, fn
                 assert "smre_oracle" not in txt and "liboracle" not in txt, fn
+
+
+def test_admm_rejects_bad_parameters(smre):
+    # validation happens before any CUDA call
+    p = smre.make_params(32, 32, [1, 2])
+    for kw in ({"sigma": -1.0}, {"sigma": 1.0, "radius": 17}, {"sigma": 1.0, "rho1": 0.0},
+               {"sigma": 1.0, "gamma": 1.0}, {"sigma": 1.0, "max_iters": 0},
+               {"sigma": 1.0, "tv_iters": -1}):
+        with pytest.raises(smre.SmreError) as ei:
+            smre.smre_admm_create(p, smre.make_admm_params(**kw))
+        assert ei.value.status == smre.SMRE_EINVAL
