@@ -8,7 +8,10 @@
     python -m paper_1503_03492_gb300.profile_cases batch512 [--images 8] [--q fp32|bf16|fp16] [--cycles 3]
         a batch of copies of that image (one step-kernel launch per group);
     python -m paper_1503_03492_gb300.profile_cases uneven [--images 32] [--q bf16] [--cycles 2]
-        the first images of the uneven 256-image batch (sides 128..1024, half 2:1).
+        the first images of the uneven 256-image batch (sides 128..1024, half 2:1);
+    python -m paper_1503_03492_gb300.profile_cases admm512 [--iters 3] [--cycles 20]
+        the ADMM outer loop on the same image (PSF sigma 2, 20 TV steps per
+        iteration, a fixed number of projection cycles per eps-step).
 
 Each prints the device time it measured.  Inputs are the seeded synthetic
 images of ``synthetic``; nothing is timed that the library does not run.
@@ -28,7 +31,8 @@ QTYPES = {"fp32": 0, "bf16": 1, "fp16": 2}
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["standard512", "icd512", "batch512", "uneven"])
+    ap.add_argument("case", choices=["standard512", "icd512", "batch512", "uneven", "admm512"])
+    ap.add_argument("--iters", type=int, default=3)
     ap.add_argument("--cycles", type=int, default=None)
     ap.add_argument("--images", type=int, default=None)
     ap.add_argument("--q", choices=list(QTYPES), default="fp32")
@@ -53,6 +57,16 @@ def main(argv=None):
             else:
                 r = P.project_incomplete(xd, out, K=3, tol=1e-3)
                 print(f"icd512: {r.cycles} sweeps, {r.seconds * 1e3:.3f} ms")
+        return 0
+    if a.case == "admm512":
+        I = torch.from_numpy(x0).cuda()
+        x = torch.empty_like(I)
+        with smre.Admm(512, 512, sides, 2.0, tv_iters=20, max_iters=a.iters, delta=-1.0,
+                       cmode=smre.SMRE_C_EXPLICIT, c_explicit=cS, max_cycles=a.cycles or 20,
+                       tol=-1.0) as A:
+            r = A.solve(I, x)
+        print(f"admm512: {r.iters} iterations, {r.seconds * 1e3:.3f} ms "
+              f"(projection {r.projection_seconds * 1e3:.3f} ms)")
         return 0
     if a.case == "batch512":
         xs = [torch.from_numpy(x0).cuda() for _ in range(a.images or 8)]
