@@ -381,7 +381,10 @@ SMRE_API void smre_server_destroy(smre_server *s);
  *   x   <- x - (1/gamma) [ -A(rho1 (I - A x - eps) + Y1) + rho2 (x - z) + Y2 ]
  *          (the linearised x-step, gamma >= rho1 + rho2)
  *   eps <- P_G(I - A x + Y1 / rho1)      (the projection of this library, from
- *          q = 0, with the cycle cap / tolerance of the smre_params)
+ *          q = 0, with the cycle cap / tolerance of the smre_params; or, with
+ *          eps_incomplete, its incomplete Dykstra approximation of Sec. 3.2,
+ *          smre_dykstra_project_incomplete(icd_K, icd_tol), as in the paper's
+ *          timings of the estimator)
  *   z   <- prox_{R / rho2}(x + Y2 / rho2) by tv_iters steps of projected
  *          gradient on the dual, p <- clip(p + (rho2/8) D(f - D^T p / rho2), -1, 1),
  *          z = f - D^T p / rho2, p kept from one iteration to the next
@@ -397,6 +400,9 @@ typedef struct {
     int tv_iters;               /* dual steps of the TV prox per iteration, >= 0   */
     int max_iters;              /* iteration cap, >= 1                             */
     double delta;               /* stopping tolerance; < 0: exactly max_iters      */
+    int eps_incomplete;         /* 0: standard projection; 1: incomplete Dykstra   */
+    int icd_K;                  /* incomplete eps-step: K (< 0: floor(log2 max side)) */
+    double icd_tol;             /* incomplete eps-step: per-tile L1 tolerance       */
 } smre_admm_params;
 
 typedef struct {
@@ -404,7 +410,8 @@ typedef struct {
     int status;                 /* OK, or ENOTCONVERGED (delta >= 0, cap reached)  */
     double dx;                  /* |x_r - x_{r-1}|_2 of the last iteration         */
     double residual;            /* |I - A x_r - eps_r|_2 of the last iteration     */
-    long long dykstra_cycles;   /* cycles of all eps-steps together                */
+    long long dykstra_cycles;   /* cycles of all eps-steps together (incomplete:
+                                   tile sweeps, summed over the tiles)              */
     double seconds;             /* wall time of the solve (host clock, synchronised) */
     double projection_seconds;  /* device time of the eps-steps alone             */
 } smre_admm_result;

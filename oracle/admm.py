@@ -37,6 +37,8 @@ import math
 import numpy as np
 
 from . import dykstra as _dykstra
+from . import icd as _icd
+from . import icd_K as _icd_K
 
 
 # ------------------------------------------------------------------ operator A
@@ -137,7 +139,7 @@ class AdmmResult:
 
 def admm(I, sides, cS, sigma, radius=0, rho1=1.0, rho2=1.0, gamma=0.0, tv_iters=20,
          max_iters=100, delta=-1.0, dyk_cycles=200, dyk_tol=-1.0, dyk_relative=False,
-         n_threads=1) -> AdmmResult:
+         n_threads=1, eps_incomplete=False, icd_K=-1, icd_tol=1e-3, icd_max_sweeps=1000) -> AdmmResult:
     """Algorithm 1 on Eq. 3 as read in the module docstring.
 
     ``gamma <= 0`` takes 1.01 (rho1 + rho2) (|A| <= 1 for a normalised
@@ -145,11 +147,17 @@ def admm(I, sides, cS, sigma, radius=0, rho1=1.0, rho2=1.0, gamma=0.0, tv_iters=
     iterations.  The eps-step runs Dykstra from q = 0 with ``dyk_cycles`` /
     ``dyk_tol`` / ``dyk_relative`` (``dyk_tol < 0``: exactly dyk_cycles).
     Start: x = z = eps = Y1 = Y2 = 0, TV dual p = 0 (carried across
-    iterations).
+    iterations).  ``eps_incomplete`` replaces the eps-step by the incomplete
+    Dykstra of Sec. 3.2 (K = ``icd_K``, floor(log2 max side) if < 0; bound of
+    side 2^k from ``cS``), the approximation the paper times the estimator with.
     """
     I = np.asarray(I, dtype=np.float64)
     H, W = I.shape
     w = gaussian_kernel(sigma, radius)
+    cmap = cS if isinstance(cS, dict) else {int(L): float(c) for L, c in zip(sides, cS)}
+    if eps_incomplete:
+        K = icd_K if icd_K >= 0 else _icd_K(sides)
+        c_level = [cmap[1 << k] for k in range(K + 1)]
     if gamma <= 0:
         gamma = 1.01 * (rho1 + rho2)
     x = np.zeros((H, W))
@@ -168,10 +176,14 @@ def admm(I, sides, cS, sigma, radius=0, rho1=1.0, rho2=1.0, gamma=0.0, tv_iters=
         x_new = x - g / gamma
         # eps-step: projection of I - A x + Y1 / rho1 onto the multi-resolution set
         Ax = blur(x_new, w)
-        r = _dykstra(I - Ax + Y1 / rho1, sides, cS, max_cycles=dyk_cycles, tol=dyk_tol,
-                     tol_relative=dyk_relative, n_threads=n_threads)
+        if eps_incomplete:
+            r = _icd(I - Ax + Y1 / rho1, K, c_level, tol=icd_tol, max_sweeps=icd_max_sweeps)
+            cycles.append(int(sum(int(sw.sum()) for sw in r.sweeps)))
+        else:
+            r = _dykstra(I - Ax + Y1 / rho1, sides, cS, max_cycles=dyk_cycles, tol=dyk_tol,
+                         tol_relative=dyk_relative, n_threads=n_threads)
+            cycles.append(r.cycles)
         eps = r.x
-        cycles.append(r.cycles)
         # z-step: prox of R / rho2 at x + Y2 / rho2
         z, p1, p2 = tv_prox(x_new + Y2 / rho2, rho2, tv_iters, p1, p2)
         # multipliers

@@ -116,7 +116,8 @@ class smre_server_counters(ctypes.Structure):
 class smre_admm_params(ctypes.Structure):
     _fields_ = [("sigma", ctypes.c_double), ("radius", ctypes.c_int), ("rho1", ctypes.c_double),
                 ("rho2", ctypes.c_double), ("gamma", ctypes.c_double), ("tv_iters", ctypes.c_int),
-                ("max_iters", ctypes.c_int), ("delta", ctypes.c_double)]
+                ("max_iters", ctypes.c_int), ("delta", ctypes.c_double),
+                ("eps_incomplete", ctypes.c_int), ("icd_K", ctypes.c_int), ("icd_tol", ctypes.c_double)]
 
 
 class smre_admm_result(ctypes.Structure):
@@ -675,11 +676,12 @@ class Server:
 # --------------------------------------------------------------------- ADMM
 
 def make_admm_params(sigma, radius=0, rho1=1.0, rho2=1.0, gamma=0.0, tv_iters=20, max_iters=100,
-                     delta=-1.0) -> smre_admm_params:
+                     delta=-1.0, eps_incomplete=False, icd_K=-1, icd_tol=1e-3) -> smre_admm_params:
     p = smre_admm_params()
     p.sigma, p.radius = float(sigma), int(radius)
     p.rho1, p.rho2, p.gamma = float(rho1), float(rho2), float(gamma)
     p.tv_iters, p.max_iters, p.delta = int(tv_iters), int(max_iters), float(delta)
+    p.eps_incomplete, p.icd_K, p.icd_tol = int(bool(eps_incomplete)), int(icd_K), float(icd_tol)
     return p
 
 
@@ -733,7 +735,8 @@ class Admm:
     Keywords of ``make_params`` set the eps-step's projection (cycle cap,
     tolerance, bounds); those of ``make_admm_params`` the outer loop."""
 
-    _AKEYS = ("radius", "rho1", "rho2", "gamma", "tv_iters", "max_iters", "delta")
+    _AKEYS = ("radius", "rho1", "rho2", "gamma", "tv_iters", "max_iters", "delta", "eps_incomplete",
+              "icd_K", "icd_tol")
 
     def __init__(self, H, W, sides, sigma, stream=None, **kw):
         akw = {k: kw.pop(k) for k in list(kw) if k in self._AKEYS}

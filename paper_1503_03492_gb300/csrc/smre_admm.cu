@@ -8,7 +8,8 @@
 //            of |x_new - x|^2 (FP64);
 //   blur   : A x_new (tile + halo), kept for the next iteration's x-step, and
 //            the projection's input s = I - A x_new + Y1 / rho1;
-//   the eps-step: smre_dykstra_project(s -> eps) on the owned projection handle;
+//   the eps-step: smre_dykstra_project(s -> eps) on the owned projection handle
+//            (or its incomplete variant, smre_dykstra_project_incomplete);
 //   tv     : one projected-gradient step on the dual of the TV prox (tile with
 //            a one-pixel halo of p and f = x + Y2 / rho2), ping-pong buffers;
 //   final  : z = f - D^T p / rho2, the multiplier steps and the block's share
@@ -303,6 +304,8 @@ smre_status smre_admm_create(const smre_params *proj, const smre_admm_params *ap
     if (ap->tv_iters < 0) return afail(nullptr, SMRE_EINVAL, "tv_iters must be >= 0");
     if (ap->max_iters < 1) return afail(nullptr, SMRE_EINVAL, "max_iters must be >= 1");
     if (std::isnan(ap->delta) || std::isnan(ap->gamma)) return afail(nullptr, SMRE_EINVAL, "delta / gamma is NaN");
+    if (ap->eps_incomplete && !(ap->icd_tol >= 0.0))
+        return afail(nullptr, SMRE_EINVAL, "icd_tol must be >= 0");
     const double gamma = ap->gamma > 0.0 ? ap->gamma : 1.01 * (ap->rho1 + ap->rho2);
     if (gamma < ap->rho1 + ap->rho2)
         return afail(nullptr, SMRE_EINVAL, "gamma %g below rho1 + rho2 = %g (the x-step would not converge)",
@@ -389,7 +392,10 @@ smre_status smre_admm_solve(smre_admm *a, const float *I, float *x, float *z, fl
         ACK(a, cudaGetLastError());
         a->launches += 2;
         smre_result pr{};
-        const smre_status ps = smre_dykstra_project(a->proj, a->s, a->eps, &pr);
+        const smre_status ps = a->ap.eps_incomplete
+                                   ? smre_dykstra_project_incomplete(a->proj, a->s, a->eps, a->ap.icd_K,
+                                                                     a->ap.icd_tol, &pr)
+                                   : smre_dykstra_project(a->proj, a->s, a->eps, &pr);
         if (ps != SMRE_OK && ps != SMRE_ENOTCONVERGED)
             return afail(a, ps, "eps-step (projection): %s", smre_last_error(a->proj));
         cycles += pr.cycles;

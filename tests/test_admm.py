@@ -75,6 +75,27 @@ def test_admm_matches_oracle(H, W, sides, sigma, radius, iters, tv_iters):
     assert res.residual == pytest.approx(ref.hist[-1, 1], rel=1e-3, abs=1e-6)
 
 
+def test_admm_incomplete_eps_step_matches_oracle():
+    # the eps-step by the incomplete Dykstra (Sec. 3.2), K = 2, tol 0 (every
+    # tile sweeps to the cap of 4 unless a sweep changes nothing)
+    H, W, sides, sigma, iters = 40, 72, [1, 2, 4], 1.0, 3
+    I = _image(H, W, sigma, seed=99)
+    cS = oracle.bounds(sides, 0.9)
+    Id = torch.from_numpy(I).cuda()
+    x, z, e = (torch.empty_like(Id) for _ in range(3))
+    with smre.Admm(H, W, sides, sigma, tv_iters=5, max_iters=iters, delta=-1.0, eps_incomplete=True,
+                   icd_K=2, icd_tol=0.0, cmode=smre.SMRE_C_EXPLICIT, c_explicit=list(cS),
+                   icd_max_sweeps=4) as A:
+        res = A.solve(Id, x, z, e)
+    ref = OA.admm(I.astype(np.float64), sides, cS, sigma=sigma, tv_iters=5, max_iters=iters,
+                  eps_incomplete=True, icd_K=2, icd_tol=0.0, icd_max_sweeps=4)
+    assert abs(res.dykstra_cycles - sum(ref.dykstra_cycles)) <= 0.01 * sum(ref.dykstra_cycles)
+    tol = TOL_PER_ITER * iters
+    assert _rel(x.cpu().numpy(), ref.x) <= tol
+    assert _rel(z.cpu().numpy(), ref.z) <= tol
+    assert _rel(e.cpu().numpy(), ref.eps) <= tol
+
+
 def test_admm_full_size_emitter_image():
     # the 512 x 512 emitter residual with the PSF of its generator (sigma 2),
     # sides 1..8, three iterations of 20 projection cycles
