@@ -412,6 +412,20 @@ def bench_admm(smre, torch, stream, threads, iters=10):
         "ms_per_iteration": 1e3 * ri.seconds / ri.iters,
         "projection_share": ri.projection_seconds / ri.seconds,
         "speedup_vs_standard_eps_step": r.seconds / ri.seconds}
+    # the FP64 oracle beside it: two iterations with each eps-step, same settings
+    t = time.perf_counter()
+    ro = oadmm.admm(x_h.astype(np.float64), SIDES, cS, sigma=2.0, tv_iters=20, max_iters=2,
+                    dyk_cycles=200, dyk_tol=1e-3, dyk_relative=True, n_threads=threads)
+    t_std = (time.perf_counter() - t) / ro.iters
+    t = time.perf_counter()
+    ri_o = oadmm.admm(x_h.astype(np.float64), SIDES, cS, sigma=2.0, tv_iters=20, max_iters=2,
+                      eps_incomplete=True, icd_K=ICD_K, icd_tol=ICD_TOL)
+    t_icd = (time.perf_counter() - t) / ri_o.iters
+    out["oracle"] = {"kind": "oracle", "cores": threads,
+                     "ms_per_iteration_standard_eps_step": 1e3 * t_std,
+                     "ms_per_iteration_incomplete_eps_step": 1e3 * t_icd,
+                     "sample": "2 iterations each (FP64 numpy + C; Dykstra on all cores, the incomplete "
+                               "step single-threaded)"}
     xs, es = torch.empty_like(I), torch.empty_like(I)
     with smre.Admm(H, W, SIDES, 2.0, tv_iters=20, max_iters=3, delta=-1.0, max_cycles=20,
                    tol=-1.0, **kw) as A:
