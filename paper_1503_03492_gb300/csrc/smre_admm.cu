@@ -10,8 +10,9 @@
 //            the projection's input s = I - A x_new + Y1 / rho1;
 //   the eps-step: smre_dykstra_project(s -> eps) on the owned projection handle
 //            (or its incomplete variant, smre_dykstra_project_incomplete);
-//   tv     : one projected-gradient step on the dual of the TV prox (tile with
-//            a one-pixel halo of p and f = x + Y2 / rho2), ping-pong buffers;
+//   tv     : up to four projected-gradient steps on the dual of the TV prox
+//            per launch (tile with a four-pixel halo of p and f = x + Y2 / rho2
+//            in shared memory), ping-pong buffers between launches;
 //   final  : z = f - D^T p / rho2, the multiplier steps and the block's share
 //            of |I - A x - eps|^2 (FP64).
 // The block partial sums are added on the host in block order, so the norms
@@ -20,6 +21,7 @@
 // of a 512 x 512 problem (1 MB each) stay in L2 between the launches.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -38,6 +40,7 @@ constexpr int kTile = 32;            // output tile (pixels per side)
 constexpr int kRows = 8;             // threads per tile column (block 32 x 8)
 constexpr int kMaxR = 16;            // largest PSF radius
 constexpr int kSpan = kTile + 2 * kMaxR;
+constexpr int kTvSteps = 4;          // TV dual steps per launch (halo of the tile)
 
 struct AdmmArgs {
     const float *I;
@@ -46,6 +49,7 @@ struct AdmmArgs {
     float *p1n, *p2n;                // TV dual, written (tv step)
     double *part;                    // one partial sum per block
     int H, W, r;
+    int tv_steps;                    // steps of this tv launch (1..kTvSteps)
     float rho1, rho2, inv_rho1, inv_rho2, inv_gamma, tau;
     float w[2 * kMaxR + 1];          // PSF weights per axis, k = -r..r
 };
@@ -160,48 +164,72 @@ __device__ __forceinline__ float dtp(float a_up, float a, float b_left, float b,
     return o;
 }
 
-// p <- clip(p + tau D(f - D^T p / rho2), -1, 1),  f = x + Y2 / rho2
+// tv_steps (1..kTvSteps) steps of p <- clip(p + tau D(f - D^T p / rho2), -1, 1),
+// f = x + Y2 / rho2, in one launch: the block loads p and f on its tile with a
+// kTvSteps-pixel halo and runs the steps in shared memory; each step needs
+// the previous one's p within one pixel, so the region still exact shrinks by
+// one pixel a side per step and the tile itself stays exact.  Every value is
+// computed with the same operations as by one launch per step.
 __global__ void __launch_bounds__(kTile * kRows) tv_kernel(const AdmmArgs A)
 {
-    // p on rows i0-1 .. i0+32, columns j0-1 .. j0+32; t on rows i0 .. i0+32,
-    // columns j0 .. j0+32 (the point and its lower / right neighbours)
-    __shared__ float P1[kTile + 2][kTile + 3], P2[kTile + 2][kTile + 3];
-    __shared__ float T[kTile + 1][kTile + 2];
-    const int i0 = blockIdx.y * kTile, j0 = blockIdx.x * kTile;
+    constexpr int R = kTile + 2 * kTvSteps;
+    __shared__ float P1[2][R][R + 1], P2[2][R][R + 1];
+    __shared__ float F[R][R + 1], T[R][R + 1];
+    const int i0 = blockIdx.y * kTile - kTvSteps, j0 = blockIdx.x * kTile - kTvSteps;
     const int tid = threadIdx.y * kTile + threadIdx.x;
     const int H = A.H, W = A.W;
-    for (int e = tid; e < (kTile + 2) * (kTile + 2); e += kTile * kRows) {
-        const int ii = e / (kTile + 2), jj = e - ii * (kTile + 2);
-        const int gi = i0 - 1 + ii, gj = j0 - 1 + jj;
+    for (int e = tid; e < R * R; e += kTile * kRows) {
+        const int u = e / R, v = e - u * R;
+        const int gi = i0 + u, gj = j0 + v;
         const bool in = gi >= 0 && gi < H && gj >= 0 && gj < W;
-        P1[ii][jj] = in ? A.p1[(size_t)gi * W + gj] : 0.f;
-        P2[ii][jj] = in ? A.p2[(size_t)gi * W + gj] : 0.f;
+        const size_t g = in ? (size_t)gi * W + gj : 0;
+        P1[0][u][v] = in ? A.p1[g] : 0.f;   // p is zero outside the image
+        P2[0][u][v] = in ? A.p2[g] : 0.f;
+        F[u][v] = in ? fmaf(A.Y2[g], A.inv_rho2, A.x[g]) : 0.f;
     }
     __syncthreads();
-    for (int e = tid; e < (kTile + 1) * (kTile + 1); e += kTile * kRows) {
-        const int ii = e / (kTile + 1), jj = e - ii * (kTile + 1);
-        const int gi = i0 + ii, gj = j0 + jj;
-        float t = 0.f;
-        if (gi < H && gj < W) {
-            const size_t g = (size_t)gi * W + gj;
-            const float f = fmaf(A.Y2[g], A.inv_rho2, A.x[g]);
-            const float d = dtp(P1[ii][jj + 1], P1[ii + 1][jj + 1], P2[ii + 1][jj], P2[ii + 1][jj + 1], gi, gj, H, W);
-            t = f - d * A.inv_rho2;
+    int c = 0;
+    for (int st = 1; st <= A.tv_steps; ++st) {
+        // p is exact on [st - 1, R - st + 1); t = f - D^T p / rho2 on [st, R - st + 1)
+        const int lo = st, hi = R - st + 1, n = hi - lo;
+        for (int e = tid; e < n * n; e += kTile * kRows) {
+            const int u = lo + e / n, v = lo + e % n;
+            const int gi = i0 + u, gj = j0 + v;
+            float t = 0.f;
+            if (gi >= 0 && gi < H && gj >= 0 && gj < W) {
+                const float d = dtp(P1[c][u - 1][v], P1[c][u][v], P2[c][u][v - 1], P2[c][u][v], gi, gj, H, W);
+                t = F[u][v] - d * A.inv_rho2;
+            }
+            T[u][v] = t;
         }
-        T[ii][jj] = t;
+        __syncthreads();
+        // the new p on [st, R - st)
+        const int m = n - 1;
+        for (int e = tid; e < m * m; e += kTile * kRows) {
+            const int u = lo + e / m, v = lo + e % m;
+            const int gi = i0 + u, gj = j0 + v;
+            float a = 0.f, b = 0.f;
+            if (gi >= 0 && gi < H && gj >= 0 && gj < W) {
+                const float tc = T[u][v];
+                const float g1 = gi <= H - 2 ? T[u + 1][v] - tc : 0.f;
+                const float g2 = gj <= W - 2 ? T[u][v + 1] - tc : 0.f;
+                a = fminf(1.f, fmaxf(-1.f, fmaf(A.tau, g1, P1[c][u][v])));
+                b = fminf(1.f, fmaxf(-1.f, fmaf(A.tau, g2, P2[c][u][v])));
+            }
+            P1[c ^ 1][u][v] = a;
+            P2[c ^ 1][u][v] = b;
+        }
+        __syncthreads();
+        c ^= 1;
     }
-    __syncthreads();
 #pragma unroll
     for (int k = 0; k < kTile / kRows; ++k) {
-        const int ii = threadIdx.y + kRows * k, jj = threadIdx.x;
-        const int gi = i0 + ii, gj = j0 + jj;
+        const int u = kTvSteps + threadIdx.y + kRows * k, v = kTvSteps + threadIdx.x;
+        const int gi = i0 + u, gj = j0 + v;
         if (gi < H && gj < W) {
-            const float tc = T[ii][jj];
-            const float g1 = gi <= H - 2 ? T[ii + 1][jj] - tc : 0.f;
-            const float g2 = gj <= W - 2 ? T[ii][jj + 1] - tc : 0.f;
             const size_t g = (size_t)gi * W + gj;
-            A.p1n[g] = fminf(1.f, fmaxf(-1.f, fmaf(A.tau, g1, P1[ii + 1][jj + 1])));
-            A.p2n[g] = fminf(1.f, fmaxf(-1.f, fmaf(A.tau, g2, P2[ii + 1][jj + 1])));
+            A.p1n[g] = P1[c][u][v];
+            A.p2n[g] = P2[c][u][v];
         }
     }
 }
@@ -400,20 +428,23 @@ smre_status smre_admm_solve(smre_admm *a, const float *I, float *x, float *z, fl
             return afail(a, ps, "eps-step (projection): %s", smre_last_error(a->proj));
         cycles += pr.cycles;
         proj_s += pr.seconds;
-        for (int k = 0; k < a->ap.tv_iters; ++k) {
+        int tv_launches = 0;
+        for (int k = 0; k < a->ap.tv_iters; k += kTvSteps) {
+            A.tv_steps = std::min(kTvSteps, a->ap.tv_iters - k);
             A.p1 = a->p1[cur];
             A.p2 = a->p2[cur];
             A.p1n = a->p1[cur ^ 1];
             A.p2n = a->p2[cur ^ 1];
             tv_kernel<<<grid, block, 0, a->stream>>>(A);
             cur ^= 1;
+            ++tv_launches;
         }
         A.p1 = a->p1[cur];
         A.p2 = a->p2[cur];
         A.part = a->d_part + a->blocks;
         final_kernel<<<grid, block, 0, a->stream>>>(A);
         ACK(a, cudaGetLastError());
-        a->launches += a->ap.tv_iters + 1;
+        a->launches += tv_launches + 1;
         ACK(a, cudaMemcpyAsync(a->h_part, a->d_part, sizeof(double) * 2 * a->blocks,
                                cudaMemcpyDeviceToHost, a->stream));
         ACK(a, cudaStreamSynchronize(a->stream));
