@@ -17,13 +17,16 @@
 // Inside a CTA a producer warp streams each item's blocks -- the k L rows of
 // x, then the increment block of every pass (and, for BF16/FP16 increments,
 // the per-window scales) -- into a byte ring of shared memory with bulk
-// asynchronous copies (TMA engine), as far ahead as the ring allows.  The 704
-// consumer threads keep the item's x in registers (thread t owns columns
-// t + 704 j), form y = x + q, the column sums of y^2 and, through shared
-// memory, the window sums in a fixed column order (the same order as the
-// single-image kernels, so FP32 results agree bit for bit), take the ball
-// test and write x (at the item's end) and the new increments straight to
-// HBM.
+// asynchronous copies (TMA engine), as far ahead as the ring allows.  The 512
+// consumer threads keep the item's x in registers (thread t owns the column
+// pairs 2 (t + 512 j), FP32x2 arithmetic), form y = x + q and the column sums
+// of y^2 in shared memory; after a barrier every consumer thread takes some
+// of the pass's windows, sums their column sums in a fixed column order (the
+// same order as the single-image kernels, so FP32 results agree bit for bit),
+// takes the ball test and leaves the window's factors in shared memory; every
+// column then applies its window's factors.  The new increments go back into
+// the ring chunk, which a storer warp copies to HBM with bulk stores; x goes
+// to HBM at the item's end.
 //
 // Mixed precision (BF16 / FP16 increments): each window's increment block is
 // stored as q_s = sw * h with h in the 16-bit type and sw a power of two per
@@ -137,9 +140,10 @@ __device__ __forceinline__ float pow2_above(float v, int shift, int &ex)
     return __uint_as_float((unsigned)r << 23);
 }
 
-// What the columns of a window need from its leader: the scale of the ball
-// test (FP32 increments), or f = (1 - scale) / sw and the power-of-two sw
-// (16-bit increments: q_i / sw = f y_i, x_i = y_i - sw h_i).
+// What the columns of a window need from the thread that took its window
+// sum: the scale of the ball test (FP32 increments), or f = (1 - scale) / sw
+// and the power-of-two sw (16-bit increments: q_i / sw = f y_i,
+// x_i = y_i - sw h_i).
 template <bool MIXED>
 struct WinData;
 template <>
