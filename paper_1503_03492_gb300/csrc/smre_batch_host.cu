@@ -8,6 +8,12 @@
 // per-window scales (16-bit types), the plane offset tables, the per-cycle
 // history and the norm partials.  Admission fails softly (slot -1) when the
 // slots or the arena are full, so a caller can wait for retirements.
+//
+// Items of a group are at most ceil(units / SMs) window-rows, so a few small
+// images still spread over every SM.  The launches of one cycle (every
+// group's step kernel, the norm and the decide kernel) are captured once into
+// a CUDA graph on a private stream and replayed each cycle; admission,
+// retirement or a new stopping rule rebuild the tables and the graph.
 #include <cuda_runtime.h>
 
 #include <algorithm>
