@@ -56,6 +56,19 @@ def rank_env():
     return r, ws, lr
 
 
+def replica_totals(dist, device, seconds, units):
+    """Whole-job figures of N replicas (one image per rank, no data exchange
+    between ranks): the time is the slowest rank's, the work the sum over the
+    ranks.  Returns (seconds, units)."""
+    import torch
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    w = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    if dist is not None and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(w, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(w.item())
+
+
 def make_input(seed):
     from synthetic import emitter_residual
     return np.ascontiguousarray(emitter_residual(H, W, n_emitters=400, seed=seed), np.float32)
@@ -517,16 +530,12 @@ def main():
             std_windows += r1.windows
             icd_windows += r2.windows
         torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
     launches = P.kernel_launches() - launches0
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    t_local = sum(step_ms) / 1e3
-    t = torch.tensor([t_local], dtype=torch.float64, device=dev)
-    w = torch.tensor([float(std_windows + icd_windows)], dtype=torch.float64, device=dev)
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(w, op=dist.ReduceOp.SUM)
-    t_max = float(t.item())
-    value = float(w.item()) / t_max
+    t_max, w_all = replica_totals(dist, dev, sum(step_ms) / 1e3, std_windows + icd_windows)
+    value = w_all / t_max
 
     # end to end through the public API with host buffers (pinned), copies inside
     x_host = torch.from_numpy(x0.copy()).pin_memory()
@@ -542,6 +551,7 @@ def main():
         b = P.project_incomplete(x_host.numpy(), o2.numpy(), K=ICD_K, tol=ICD_TOL)
         e2e_t += time.perf_counter() - t0
         e2e_w += a.windows + b.windows
+    e2e_t, e2e_w = replica_totals(dist, dev, e2e_t, e2e_w)
     e2e_val = e2e_w / e2e_t
 
     peak, peak_src = measured_peak_hbm()
