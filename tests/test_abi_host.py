@@ -106,3 +106,19 @@ def test_admm_rejects_bad_parameters(smre):
         with pytest.raises(smre.SmreError) as ei:
             smre.smre_admm_create(p, smre.make_admm_params(**kw))
         assert ei.value.status == smre.SMRE_EINVAL
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    # the binding has no fallback: without libsmre.so every call raises
+    import subprocess
+    import sys
+    code = (
+        "import paper_1503_03492_gb300 as m\n"
+        f"m.lib_path = lambda: {str(tmp_path / 'libsmre.so')!r}\n"
+        "try:\n"
+        "    m.smre_version()\n"
+        "except ImportError as e:\n"
+        "    print('raised', e)\n"
+    )
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and r.stdout.startswith("raised"), r.stdout + r.stderr
