@@ -1037,6 +1037,7 @@ smre_status smre_dykstra_project_incomplete(smre_dykstra *h, const float *x0, fl
         A.max_sweeps = h->icd_max_sweeps;
         for (int k = 0; k <= K; ++k) {
             A.cS[k] = cS[k];
+            A.sqrt_cS[k] = (float)std::sqrt(cS64[k]);
             A.cS64[k] = cS64[k];
         }
         A.sweeps = h->icd_sweeps + o;

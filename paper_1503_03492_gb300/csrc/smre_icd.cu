@@ -140,13 +140,16 @@ __global__ void __launch_bounds__(IcdShape<K>::THREADS) icd_pass_kernel(const Ic
                 for (int p = 0; p < P; ++p) tsum[p] = s;
             }
 
-            // ball test; FP64 recheck of windows whose sum lies near cS
+            // ball test, scale sqrt(cS) rsqrt(t) as in the standard kernels (a
+            // tile's sweeps are one dependent chain, and an IEEE division plus
+            // square root per level doubled its length); FP64 recheck of
+            // windows whose sum lies near cS
             const float c = A.cS[k];
             float scale[P];
             bool near_any = false;
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                scale[p] = tsum[p] > c ? sqrtf(c / tsum[p]) : 1.f;
+                scale[p] = tsum[p] > c ? A.sqrt_cS[k] * rsqrtf(tsum[p]) : 1.f;
                 near_any |= fabsf(tsum[p] - c) <= kNearBand * c;
             }
             if (wpx <= P) {

@@ -237,6 +237,7 @@ struct IcdArgs {
     float tol_b2;         // tol * B^2
     int max_sweeps;
     float cS[kMaxIcdK + 1];      // bound of side 2^k
+    float sqrt_cS[kMaxIcdK + 1]; // its square root (FP32): scale = sqrt(cS) * rsqrt(t)
     double cS64[kMaxIcdK + 1];
     int *sweeps;          // per-tile sweep counts of this pass (n_ti * n_tj)
 };
