@@ -129,3 +129,22 @@ def test_admm_stopping_rule():
                    cmode=smre.SMRE_C_EXPLICIT, c_explicit=list(cS), max_cycles=20, tol=-1.0) as A:
         r = A.solve(Id, x)
         assert r.status == smre.SMRE_ENOTCONVERGED and r.iters == 2
+
+
+@pytest.mark.parametrize("q_dtype,u", [(1, 2.0 ** -8), (2, 2.0 ** -11)])
+def test_admm_with_16bit_increments(q_dtype, u):
+    # the eps-step through a projection with BF16 / FP16 increments (a
+    # one-image batch): within K times the 16-bit envelope (4 u a projection)
+    # of the same loop with FP32 increments
+    H, W, sides, sigma, iters = 40, 72, [1, 2, 4], 1.0, 3
+    I = _image(H, W, sigma, seed=5)
+    cS = oracle.bounds(sides, 0.9)
+    Id = torch.from_numpy(I).cuda()
+    outs = []
+    for qd in (0, q_dtype):
+        x = torch.empty_like(Id)
+        with smre.Admm(H, W, sides, sigma, tv_iters=5, max_iters=iters, delta=-1.0, q_dtype=qd,
+                       cmode=smre.SMRE_C_EXPLICIT, c_explicit=list(cS), max_cycles=20, tol=-1.0) as A:
+            A.solve(Id, x)
+        outs.append(x.cpu().numpy())
+    assert _rel(outs[1], outs[0]) <= iters * 4 * u
