@@ -397,16 +397,6 @@ void build_schedule(smre_dykstra *h)
     h->q_floats = (size_t)off;
 }
 
-bool is_device_ptr(const void *p)
-{
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
 smre_status ensure_hist(smre_dykstra *h, int cap)
 {
     if (cap <= h->hist_cap) return SMRE_OK;
@@ -834,7 +824,7 @@ void set_thread_error(const char *msg) { g_err = msg; }
 
 extern "C" {
 
-const char *smre_version(void) { return "smre-gb300 0.5 (sm_103a)"; }
+const char *smre_version(void) { return "smre-gb300 0.6 (sm_103a)"; }
 
 const char *smre_last_error(const smre_dykstra *h)
 {

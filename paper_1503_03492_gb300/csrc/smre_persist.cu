@@ -107,11 +107,24 @@ __device__ __forceinline__ void consumers_sync(int nthreads)
 
 __device__ __forceinline__ void cta_sync_all() { asm volatile("barrier.sync 0;" ::: "memory"); }
 
-// named barrier 2 among the warps that hold windows in the current task
-__device__ __forceinline__ void workers_sync(int nthreads)
+// named barrier 2 among the warps that hold windows in the current task,
+// returning the OR of pred over them
+__device__ __forceinline__ bool workers_sync_or(bool pred, int nthreads)
 {
-    if (nthreads == 32) __syncwarp();
-    else asm volatile("barrier.sync 2, %0;" ::"r"(nthreads) : "memory");
+    if (nthreads == 32) {
+        __syncwarp();
+        return __any_sync(0xffffffffu, pred);
+    }
+    unsigned r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "barrier.red.or.pred q, 2, %2, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((unsigned)pred), "r"(nthreads)
+        : "memory");
+    return r != 0;
 }
 
 // One offset a of a side task as the passes see it.
@@ -127,7 +140,6 @@ struct PassCtx {
     const PersistArgs *A;
     uint64_t *full, *written;
     float *stage0, *xs;
-    volatile int *pass_abort;   // shared: set by a worker whose copy did not arrive
     const long long *pass_qoff; // q offset of each pass of this CTA's cycle
     int S, NCW, NC, warp, lane, pitch;
 };
@@ -253,9 +265,8 @@ __device__ __forceinline__ bool run_passes(const PassCtx &cx, const PassTask &ts
         __syncwarp();
         if (lane == 0) mbar_arrive(&cx.written[s]);   // this warp is done reading the stage
         s_cur = s + 1 == cx.S ? 0 : s + 1;
-        if (bad) *cx.pass_abort = 1;
-        workers_sync(nwork * 32);                         // orders xs between passes
-        if (*cx.pass_abort) return true;                  // copies lost: abandon (uniformly)
+        // orders xs between passes; a copy lost anywhere abandons the launch
+        if (workers_sync_or(bad, nwork * 32)) return true;
     }
     return false;
 }
@@ -368,7 +379,6 @@ __global__ void __launch_bounds__(kPersistThreads, 1) persist_kernel(const Persi
     float *stage0 = reinterpret_cast<float *>(smem + A.stage_offset); // [S][stage_floats]
     float *xs = stage0 + (size_t)S * A.stage_floats;                  // [rows][SP]
     __shared__ int s_dec, s_abort;
-    __shared__ volatile int s_pass_abort;
     __shared__ double s_red[2][32];
 
     const int tid = threadIdx.x;
@@ -410,7 +420,6 @@ __global__ void __launch_bounds__(kPersistThreads, 1) persist_kernel(const Persi
         fence_mbar_init();
         s_dec = kGo;
         s_abort = 0;
-        s_pass_abort = 0;
     }
     __syncthreads();
 
@@ -500,14 +509,13 @@ __global__ void __launch_bounds__(kPersistThreads, 1) persist_kernel(const Persi
     }
 
     // ======================================================== consumer warps
-    const PassCtx cx{&A, full, written, stage0, xs, &s_pass_abort, pass_qoff, S, NCW, NC, warp, lane, pitch};
+    const PassCtx cx{&A, full, written, stage0, xs, pass_qoff, S, NCW, NC, warp, lane, pitch};
     int s_cur = 0;
     unsigned fph = 0;            // parity of the next `full` wait, per stage
     double d2 = 0.0, n2 = 0.0;   // this thread's share of the cycle norm
     bool aborted = false;
 
     for (int cyc = 0;; ++cyc) {
-        const bool first = cyc == 0;
         for (int si = 0; si < nside && !aborted; ++si) {
             const SideS sd = sides_s[si];
             const int L = sd.L, band = sd.U * L;
