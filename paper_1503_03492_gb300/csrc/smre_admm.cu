@@ -445,18 +445,22 @@ smre_status smre_admm_solve(smre_admm *a, const float *I, float *x, float *z, fl
         final_kernel<<<grid, block, 0, a->stream>>>(A);
         ACK(a, cudaGetLastError());
         a->launches += tv_launches + 1;
-        ACK(a, cudaMemcpyAsync(a->h_part, a->d_part, sizeof(double) * 2 * a->blocks,
-                               cudaMemcpyDeviceToHost, a->stream));
-        ACK(a, cudaStreamSynchronize(a->stream));
-        double d2 = 0.0, r2 = 0.0;
-        for (int b = 0; b < a->blocks; ++b) {
-            d2 += a->h_part[b];
-            r2 += a->h_part[a->blocks + b];
-        }
-        dx = std::sqrt(d2);
-        rr = std::sqrt(r2);
         ++it;
-        if (a->ap.delta >= 0.0 && dx <= a->ap.delta && rr <= a->ap.delta) break;
+        // the norms are needed every iteration only for the stopping test;
+        // with a fixed count they are read once, after the last iteration
+        if (a->ap.delta >= 0.0 || it == a->ap.max_iters) {
+            ACK(a, cudaMemcpyAsync(a->h_part, a->d_part, sizeof(double) * 2 * a->blocks,
+                                   cudaMemcpyDeviceToHost, a->stream));
+            ACK(a, cudaStreamSynchronize(a->stream));
+            double d2 = 0.0, r2 = 0.0;
+            for (int b = 0; b < a->blocks; ++b) {
+                d2 += a->h_part[b];
+                r2 += a->h_part[a->blocks + b];
+            }
+            dx = std::sqrt(d2);
+            rr = std::sqrt(r2);
+            if (a->ap.delta >= 0.0 && dx <= a->ap.delta && rr <= a->ap.delta) break;
+        }
     }
     if (a->ap.delta >= 0.0 && !(dx <= a->ap.delta && rr <= a->ap.delta)) status = SMRE_ENOTCONVERGED;
     ACK(a, cudaMemcpyAsync(x, a->x, sizeof(float) * n, cudaMemcpyDeviceToDevice, a->stream));
