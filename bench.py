@@ -334,20 +334,9 @@ def bench_mixed(smre, torch, stream, peak, threads):
     return out
 
 
-def bench_serving(smre, torch, stream, n_req=64, rate=500.0, slots=16):
-    """Poisson arrivals (mean `rate` per second) of square SOFI-like requests,
-    side uniform in 64..2048, window sides 1..8, BF16 increments, at most 100
-    cycles or a relative step of 1e-6: the request loop against the plain
-    single-image API (FP32, one request at a time, in arrival order)."""
-    from synthetic import request_stream, request_image, sofi_canvas
-    canvas = sofi_canvas()
-    reqs = request_stream(n=n_req, rate=rate)
-    imgs = [np.ascontiguousarray(request_image(canvas, side, sd), np.float32)
-            for (_, side, sd) in reqs]
-    arrivals = [a for (a, _, _) in reqs]
-    cS = smre.smre_bounds(smre.make_params(64, 64, SIDES, alpha=ALPHA))
-    kw = dict(cmode=smre.SMRE_C_EXPLICIT, c_explicit=cS, max_cycles=100, tol=1e-6,
-              tol_relative=True)
+def _serve(smre, stream, imgs, arrivals, kw, slots):
+    """The request loop on one arrival stream: images/s and latency quantiles
+    (submission to result, queueing included)."""
     outs = [np.empty_like(a) for a in imgs]
     with smre.Server(SIDES, cycles_per_round=4, stream=stream, q_dtype=smre.SMRE_Q_BF16,
                      max_images=slots, device_bytes=48 << 30, **kw) as S:
@@ -361,9 +350,13 @@ def bench_serving(smre, torch, stream, n_req=64, rate=500.0, slots=16):
         for t in tickets:
             S.wait(t)
         st = S.stats()
-    served = {"images_per_s": st.images_per_s, "p50_s": st.p50_s, "p99_s": st.p99_s,
-              "max_s": st.max_s, "peak_active": st.peak_active, "rounds": st.rounds}
-    # the plain path on the same stream: one request at a time, arrival order
+    return {"images_per_s": st.images_per_s, "p50_s": st.p50_s, "p99_s": st.p99_s,
+            "max_s": st.max_s, "peak_active": st.peak_active, "rounds": st.rounds}
+
+
+def _plain(smre, stream, imgs, arrivals, kw):
+    """The plain single-image API (FP32) on the same stream, one request at a
+    time in arrival order."""
     lat = []
     t0 = time.perf_counter()
     for a, img in zip(arrivals, imgs):
@@ -375,14 +368,43 @@ def bench_serving(smre, torch, stream, n_req=64, rate=500.0, slots=16):
             o = np.empty_like(img)
             P.project(img, o)
         lat.append(time.perf_counter() - t0 - a)
-    t_plain = time.perf_counter() - t0
+    t_all = time.perf_counter() - t0
     lat.sort()
-    plain = {"images_per_s": n_req / t_plain, "p50_s": lat[len(lat) // 2],
-             "p99_s": lat[min(len(lat) - 1, int(round(0.99 * (len(lat) - 1))))]}
+    return {"images_per_s": len(imgs) / t_all, "p50_s": lat[len(lat) // 2],
+            "p99_s": lat[min(len(lat) - 1, int(round(0.99 * (len(lat) - 1))))]}
+
+
+def bench_serving(smre, torch, stream, n_req=64, rate=500.0, slots=16, sweep=((5.0, 24), (15.0, 24))):
+    """Poisson arrivals (mean `rate` per second) of square SOFI-like requests,
+    side uniform in 64..2048, window sides 1..8, BF16 increments, at most 100
+    cycles or a relative step of 1e-6: the request loop against the plain
+    single-image API (FP32, one request at a time, in arrival order) -- at
+    the overloading rate (saturation throughput) and at rates below it."""
+    from synthetic import request_stream, request_image, sofi_canvas
+    canvas = sofi_canvas()
+    cS = smre.smre_bounds(smre.make_params(64, 64, SIDES, alpha=ALPHA))
+    kw = dict(cmode=smre.SMRE_C_EXPLICIT, c_explicit=cS, max_cycles=100, tol=1e-6,
+              tol_relative=True)
+
+    def stream_of(n, r):
+        reqs = request_stream(n=n, rate=r)
+        imgs = [np.ascontiguousarray(request_image(canvas, side, sd), np.float32)
+                for (_, side, sd) in reqs]
+        return imgs, [a for (a, _, _) in reqs]
+
+    imgs, arrivals = stream_of(n_req, rate)
+    served = _serve(smre, stream, imgs, arrivals, kw, slots)
+    plain = _plain(smre, stream, imgs, arrivals, kw)
+    below = []
+    for r, n in sweep:
+        im, ar = stream_of(n, r)
+        below.append({"rate_per_s": r, "requests": n, "served_bf16": _serve(smre, stream, im, ar, kw, slots),
+                      "plain_single_image_fp32": _plain(smre, stream, im, ar, kw)})
     return {"requests": n_req, "rate_per_s": rate, "sides": "1..8", "slots": slots,
             "stop": "rel step < 1e-6 or 100 cycles", "served_bf16": served,
             "plain_single_image_fp32": plain,
-            "images_per_s_ratio": served["images_per_s"] / plain["images_per_s"]}
+            "images_per_s_ratio": served["images_per_s"] / plain["images_per_s"],
+            "below_saturation": below}
 
 
 def bench_admm(smre, torch, stream, threads, iters=10):
