@@ -12,7 +12,12 @@
  *   - smre_dykstra_project runs Dykstra's cyclic projection (Sec. 2.3,
  *     Algorithm 2) to a stopping tolerance or a cycle cap;
  *   - smre_dykstra_project_incomplete runs the incomplete Dykstra variant of
- *     Sec. 3.2 (dyadic squares, passes at shifts 2^i).
+ *     Sec. 3.2 (dyadic squares, passes at shifts 2^i);
+ *   - smre_batch_* run the standard projection for many images of different
+ *     sizes in shared launches, smre_server_* serve projection requests by
+ *     continuous batching (no counterpart in the paper);
+ *   - smre_admm_* run the estimator itself: the ADMM loop of Sec. 2.2
+ *     (Algorithm 1, Eq. 3) with the projection as its eps-step.
  *
  * Conventions shared by every entry point:
  *   - Errors are returned as smre_status codes; nothing aborts, nothing throws.
