@@ -96,6 +96,13 @@ __global__ void __launch_bounds__(IcdShape<K>::THREADS) icd_pass_kernel(const Ic
         for (int k = 0; k <= K; ++k) q[k][p] = 0.f;
     }
 
+    // tiles within one warp: the level-K window is the whole tile, so the next
+    // sweep's level-K sum is formed while this sweep's change is reduced over
+    // the same lanes (two independent butterflies, each with the operations
+    // and order it has on its own)
+    constexpr bool kAheadK = TPT <= 32;
+    float tK = 0.f;
+    bool have_tK = false;
     int sweeps = 0;
     bool done = false;
     while (!done) {
@@ -110,7 +117,10 @@ __global__ void __launch_bounds__(IcdShape<K>::THREADS) icd_pass_kernel(const Ic
 
             // window sums of y^2
             float tsum[P];
-            if (wpx <= P) {
+            if (kAheadK && k == K && have_tK) {
+#pragma unroll
+                for (int p = 0; p < P; ++p) tsum[p] = tK;
+            } else if (wpx <= P) {
 #pragma unroll
                 for (int p = 0; p < P; ++p) {
                     const int w0 = (p / wpx) * wpx;
@@ -210,8 +220,21 @@ __global__ void __launch_bounds__(IcdShape<K>::THREADS) icd_pass_kernel(const Ic
 
         // tile-wide L1 change of the sweep
         float dtile;
-        if (TPT <= 32) {
-            dtile = group_sum(delta, TPT, tile_mask);
+        if (kAheadK) {
+            float s = 0.f;
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                const float yk = x[p] + q[K][p];
+                s = fmaf(yk, yk, s);
+            }
+            float d = delta;
+            for (int o = TPT >> 1; o > 0; o >>= 1) {
+                d += __shfl_xor_sync(tile_mask, d, o);
+                s += __shfl_xor_sync(tile_mask, s, o);
+            }
+            dtile = d;
+            tK = s;
+            have_tK = true;
         } else {
             float s = group_sum(delta, 32, 0xffffffffu);
             if (lane == 0) s_red[tile_in_cta][warp_in_tile] = s;
