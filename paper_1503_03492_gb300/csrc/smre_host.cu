@@ -824,7 +824,7 @@ void set_thread_error(const char *msg) { g_err = msg; }
 
 extern "C" {
 
-const char *smre_version(void) { return "smre-gb300 0.6 (sm_103a)"; }
+const char *smre_version(void) { return "smre-gb300 0.7 (sm_103a)"; }
 
 const char *smre_last_error(const smre_dykstra *h)
 {

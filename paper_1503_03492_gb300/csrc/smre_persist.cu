@@ -378,7 +378,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1) persist_kernel(const Persi
     unsigned char *tbl = smem + 512;                                  // schedule
     float *stage0 = reinterpret_cast<float *>(smem + A.stage_offset); // [S][stage_floats]
     float *xs = stage0 + (size_t)S * A.stage_floats;                  // [rows][SP]
-    __shared__ int s_dec, s_abort;
+    __shared__ int s_dec;
     __shared__ double s_red[2][32];
 
     const int tid = threadIdx.x;
@@ -419,7 +419,6 @@ __global__ void __launch_bounds__(kPersistThreads, 1) persist_kernel(const Persi
         }
         fence_mbar_init();
         s_dec = kGo;
-        s_abort = 0;
     }
     __syncthreads();
 
@@ -522,16 +521,16 @@ __global__ void __launch_bounds__(kPersistThreads, 1) persist_kernel(const Persi
 
             // side start: wait for the last publishers (other CTAs) of the rows
             // this side may read, then bring the band in
+            bool lost = false;
             if (tid == 0) {
                 bool ok = true;
                 if (A.selftest_timeout && cta == 0 && si == 0)
                     ok = wait_geq(A, A.selftest_flag, 1u);   // a flag nothing sets
                 for (int k = 0; k < sd.dep_count && ok; ++k)
                     ok = wait_geq(A, A.flags + deps_s[sd.dep_begin + k], (unsigned)(cyc + 1));
-                s_abort = ok ? 0 : 1;
+                lost = !ok;
             }
-            consumers_sync(NC);
-            if (s_abort) { aborted = true; break; }
+            if (consumers_sync_or(lost, NC)) { aborted = true; break; }
             load_rows<SP>(A, xs, 0, sd.r0, band, tid, NC);
             consumers_sync(NC);
 
@@ -541,13 +540,10 @@ __global__ void __launch_bounds__(kPersistThreads, 1) persist_kernel(const Persi
                     // the band slides down one row: drop the (published) top row,
                     // take the lower neighbour's published top row at the bottom
                     shift_rows_up<SP>(A, xs, band, tid, NC);
-                    if (tid == 0) {
-                        const bool ok = gp.nb_flag < 0 ||
-                                        wait_geq(A, A.flags + gp.nb_flag, (unsigned)(cyc + 1));
-                        s_abort = ok ? 0 : 1;
-                    }
-                    consumers_sync(NC);
-                    if (s_abort) { aborted = true; break; }
+                    bool lost = false;
+                    if (tid == 0)
+                        lost = !(gp.nb_flag < 0 || wait_geq(A, A.flags + gp.nb_flag, (unsigned)(cyc + 1)));
+                    if (consumers_sync_or(lost, NC)) { aborted = true; break; }
                     load_rows<SP>(A, xs, band - 1, sd.r0 + a - 1 + band, 1, tid, NC);
                     consumers_sync(NC);
                 }
@@ -585,6 +581,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1) persist_kernel(const Persi
                 s_red[1][warp] = bb;
             }
             consumers_sync(NC);
+            bool late = false;
             if (tid == 0) {
                 double D = 0.0, N = 0.0;
                 for (int w = 0; w < NCW; ++w) {
@@ -595,12 +592,12 @@ __global__ void __launch_bounds__(kPersistThreads, 1) persist_kernel(const Persi
                 slot[2 * (size_t)cta + 1] = N;
                 __threadfence();
                 atomicAdd(A.barrier, 1u);
-                s_abort = wait_geq(A, A.barrier, (unsigned)G * (unsigned)(cyc + 1)) ? 0 : 1;
+                late = !wait_geq(A, A.barrier, (unsigned)G * (unsigned)(cyc + 1));
             }
-            consumers_sync(NC);
+            late = consumers_sync_or(late, NC);
             d2 = 0.0;
             n2 = 0.0;
-            if (s_abort) {
+            if (late) {
                 dec = kAbort;
             } else {
                 // every CTA sums the partials in the same fixed tree, in parallel:
