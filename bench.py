@@ -145,7 +145,7 @@ class Clocks:
 # version: (first-cycle bytes, bytes per later cycle).  A version without an
 # entry reports traffic as null until it is captured again.
 MEASURED_TRAFFIC = {
-    "smre-gb300 0.6 (sm_103a)": (209.2e6, 416.4e6),
+    "smre-gb300 0.7 (sm_103a)": (209.3e6, 416.5e6),
 }
 
 
