@@ -430,7 +430,8 @@ SMRE_API smre_status smre_admm_create(const smre_params *proj, const smre_admm_p
                                       void *cuda_stream, smre_admm **out);
 
 /* Run the loop on the observed image I (device, H x W).  x (required), z and
- * eps (NULL: not returned) receive the final iterates (device, H x W).
+ * eps (NULL: not returned) receive the final iterates (device, H x W).  Host
+ * pointers are rejected with EINVAL.
  * Returns OK, ENOTCONVERGED, EINVAL, ETIMEOUT or ECUDA. */
 SMRE_API smre_status smre_admm_solve(smre_admm *a, const float *I, float *x, float *z, float *eps,
                                      smre_admm_result *res);

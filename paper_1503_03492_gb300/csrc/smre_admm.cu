@@ -303,6 +303,20 @@ smre_status afail(smre_admm *a, smre_status s, const char *fmt, ...)
                          "%s: %s", #call, cudaGetErrorString(e_));                            \
     } while (0)
 
+// The solver's kernels read and write its images directly: each must be
+// device (or managed) memory, checked on the host so that a host pointer is
+// an EINVAL and not a fault.
+bool device_image(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
 void release(smre_admm *a)
 {
     if (!a) return;
@@ -395,6 +409,8 @@ smre_status smre_admm_solve(smre_admm *a, const float *I, float *x, float *z, fl
 {
     if (!a) return afail(nullptr, SMRE_EINVAL, "solver is NULL");
     if (!I || !x) return afail(a, SMRE_EINVAL, "I / x is NULL");
+    if (!device_image(I) || !device_image(x) || (z && !device_image(z)) || (eps && !device_image(eps)))
+        return afail(a, SMRE_EINVAL, "I, x, z and eps must be device images");
     const auto t0 = std::chrono::steady_clock::now();
     const size_t n = (size_t)a->H * a->W;
     ACK(a, cudaMemsetAsync(a->buf, 0, sizeof(float) * n * 11, a->stream));

@@ -148,3 +148,20 @@ def test_admm_with_16bit_increments(q_dtype, u):
             A.solve(Id, x)
         outs.append(x.cpu().numpy())
     assert _rel(outs[1], outs[0]) <= iters * 4 * u
+
+
+def test_admm_rejects_host_images():
+    # the solver's kernels use the images directly: host memory is an EINVAL
+    I = _image(32, 40, 1.0, seed=3)
+    cS = oracle.bounds([1, 2], 0.9)
+    with smre.Admm(32, 40, [1, 2], 1.0, max_iters=1, cmode=smre.SMRE_C_EXPLICIT,
+                   c_explicit=list(cS), max_cycles=2, tol=-1.0) as A:
+        x = np.empty_like(I)
+        with pytest.raises(smre.SmreError) as ei:
+            A.solve(I, x)
+        assert ei.value.status == smre.SMRE_EINVAL
+        Id = torch.from_numpy(I).cuda()
+        with pytest.raises(smre.SmreError):
+            A.solve(Id, x)
+        xd = torch.empty_like(Id)
+        A.solve(Id, xd)   # still usable
