@@ -311,3 +311,50 @@ def test_autotuned_schedule_gives_the_same_answer(smre, torch_cuda, oracle_mod):
             assert np.array_equal(out.cpu().numpy(), group)
         with smre.Projector(*shape, sides, flags=smre.SMRE_F_AUTOTUNE, **kw) as P:
             assert P.schedule() == sched          # cached for the shape
+
+
+# ------------------------------------------------------ full workload sizes
+
+def test_full_size_2048_sides_1_to_12(smre, oracle_mod):
+    # the 2048 x 2048 emitter residual (1600 emitters), sides 1..12, through
+    # the C ABI (a one-image batch: wider than the persistent kernel), 3
+    # cycles against the FP64 oracle: FP32 to the 1e-5 bar, 16-bit increments
+    # within their envelope
+    from synthetic import emitter_residual_2048
+    x0 = f32(emitter_residual_2048())
+    sides = list(range(1, 13))
+    cS = oracle_mod.bounds(sides, 0.9)
+    ref = oracle_mod.dykstra(x0.astype(np.float64), sides, cS, max_cycles=3, tol=-1, n_threads=NTH).x
+    for qdt in (0, 1, 2):
+        out = np.empty_like(x0)
+        with smre.Projector(2048, 2048, sides, cmode=smre.SMRE_C_EXPLICIT, c_explicit=list(cS),
+                            max_cycles=3, tol=-1.0, q_dtype=qdt) as P:
+            r = P.project(x0, out)
+        assert r.cycles == 3
+        # the 16-bit roundings of successive set updates are independent, so
+        # their sum grows like the square root of the updates a pixel sees per
+        # cycle: sum_L L^2 = 650 here against 204 for sides 1..8
+        bound = TOL if qdt == 0 else U16_ENVELOPE * U16[qdt] * np.sqrt(sum(L * L for L in sides) / 204.0)
+        assert err(out, ref) <= bound, (qdt, err(out, ref))
+
+
+def test_full_uneven_batch_sampled(smre, oracle_mod):
+    # the whole 256-image uneven batch (sides 128..1024, half of them 2:1) in
+    # one batch, FP32 increments, 2 cycles; a seeded sample of images against
+    # the FP64 oracle
+    from synthetic import batch_images
+    xs = [f32(a) for a in batch_images(256)]
+    sides = list(range(1, 9))
+    cS = oracle_mod.bounds(sides, 0.9)
+    params = smre.make_batch_params(sides, cmode=smre.SMRE_C_EXPLICIT, c_explicit=list(cS),
+                                    max_cycles=2, tol=-1.0)
+    need = sum(smre.smre_batch_image_bytes(params, *x.shape) for x in xs)
+    outs = [np.empty_like(x) for x in xs]
+    with smre.Batch(sides, cmode=smre.SMRE_C_EXPLICIT, c_explicit=list(cS), max_cycles=2, tol=-1.0,
+                    max_images=len(xs), device_bytes=need + (64 << 20)) as B:
+        B.project(xs, outs)
+    pick = np.random.default_rng(11).choice(len(xs), size=8, replace=False)
+    for i in pick:
+        ref = oracle_mod.dykstra(xs[i].astype(np.float64), sides, cS, max_cycles=2, tol=-1,
+                                 n_threads=NTH).x
+        assert err(outs[i], ref) <= TOL, (int(i), xs[i].shape, err(outs[i], ref))
