@@ -31,6 +31,7 @@ import json
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -90,7 +91,10 @@ class Clocks:
     def __init__(self, dev_index):
         self.dev = dev_index
         self.p = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{dev_index}.csv")
+        # the raw samples (the JSON line carries their summary); SMRE_CLOCKS_DIR
+        # chooses where they are kept
+        out_dir = os.environ.get("SMRE_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out_dir, f"smre_clocks_rank{dev_index}.csv")
 
     def __enter__(self):
         try:
