@@ -90,6 +90,11 @@ typedef enum {
                                      waits on a flag nothing sets, with a 50 ms limit,
                                      so smre_dykstra_project must return
                                      SMRE_ETIMEOUT and the handle stay usable        */
+#define SMRE_F_BAND_IN_SMEM 16    /* the persistent launch keeps each CTA's band of x
+                                     in shared memory and maps warps onto windows per
+                                     pass, even where the register-band kernel fits
+                                     (row stride <= 1024, sides <= 8, bands of <= 8
+                                     rows); same results bit for bit, slower          */
 
 /* increment storage types (smre_params.q_dtype, smre_batch_params.q_dtype) */
 #define SMRE_Q_FP32 0

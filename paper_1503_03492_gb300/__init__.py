@@ -19,7 +19,8 @@ import os
 __all__ = [
     "SMRE_OK", "SMRE_EINVAL", "SMRE_ENOMEM", "SMRE_ECUDA", "SMRE_ETIMEOUT", "SMRE_ENOTCONVERGED",
     "SMRE_C_PERSET", "SMRE_C_CHI2", "SMRE_C_MAXSTAT", "SMRE_C_EXPLICIT", "SMRE_F_VIOLATION",
-    "SMRE_F_GROUP_LAUNCHES", "SMRE_F_SELFTEST_TIMEOUT", "SMRE_F_AUTOTUNE", "SMRE_SCHED_PERSISTENT",
+    "SMRE_F_GROUP_LAUNCHES", "SMRE_F_SELFTEST_TIMEOUT", "SMRE_F_AUTOTUNE", "SMRE_F_BAND_IN_SMEM",
+    "SMRE_SCHED_PERSISTENT",
     "SMRE_SCHED_BATCHED", "SMRE_SCHED_GROUPS", "smre_dykstra_schedule",
     "SmreError", "smre_params", "smre_result", "lib_path", "load",
     "smre_bounds", "smre_dykstra_create", "smre_dykstra_project",
@@ -44,6 +45,7 @@ SMRE_F_VIOLATION = 1
 SMRE_F_GROUP_LAUNCHES = 2
 SMRE_F_SELFTEST_TIMEOUT = 4
 SMRE_F_AUTOTUNE = 8
+SMRE_F_BAND_IN_SMEM = 16
 SMRE_SCHED_PERSISTENT, SMRE_SCHED_BATCHED, SMRE_SCHED_GROUPS = 1, 2, 3
 SMRE_Q_FP32, SMRE_Q_BF16, SMRE_Q_FP16 = range(3)
 

@@ -73,13 +73,17 @@ struct smre_dykstra {
     int p_grid = 0, p_threads = 0, p_stages = 0, p_ncw = 0, p_maxL = 0;
     size_t p_smem = 0;
     int p_stage_floats = 0, p_stage_offset = 0, p_sp = 0;
-    int n_tasks = 0;
+    bool p_reg = false;            // the register-band kernel (else the shared-memory band)
+    int n_tasks = 0;               // flags: events x (consumer warps of the register kernel)
     unsigned char *d_sched = nullptr;
     int *d_cta_off = nullptr;
     int p_sched_bytes = 0;
     unsigned *d_flags = nullptr, *d_barrier = nullptr, *d_selftest = nullptr;
     double *d_ppartials = nullptr;
     float *d_zeros = nullptr;
+    unsigned long long *d_xch = nullptr;   // register kernel: tagged transition rows
+    unsigned tag_next = 1;                 // tag base of the next persistent launch
+    size_t xch_words = 0;
     int *d_abort = nullptr;
     unsigned long long timeout_ns = 10000000000ull;
     std::string err;
@@ -570,6 +574,8 @@ smre_status plan_persistent(smre_dykstra *h, int flags)
     int max_items = 1;
     double items_ratio = 0.0;
     long long stage_floats = 0;
+    long long stage_floats_reg = 0;   // U L pitch: the register kernel's stages are packed rows
+    int max_band = 0;
     size_t seg_max = 16;
     for (int c = 0; c < G; ++c) {
         std::vector<SideS> ss;
@@ -612,6 +618,8 @@ smre_status plan_persistent(smre_dykstra *h, int flags)
             max_items = std::max(max_items, items);
             items_ratio = std::max(items_ratio, (double)items / max_items_for_side(L));
             stage_floats = std::max(stage_floats, (long long)U * L * sp);
+            stage_floats_reg = std::max(stage_floats_reg, (long long)U * L * pitch);
+            max_band = std::max(max_band, U * L);
         }
         const int hdr[4] = {(int)ss.size(), (int)gs.size(), (int)qo.size(), (int)dl.size()};
         const size_t bytes = sizeof(hdr) + sizeof(SideS) * ss.size() + sizeof(GrpS) * gs.size() +
@@ -634,23 +642,60 @@ smre_status plan_persistent(smre_dykstra *h, int flags)
     }
 
     if (!persist_supported(maxL)) return SMRE_OK;
-    const int ncw = std::max(4, std::min(kPersistThreads / 32 - 1, max_items));
-    if (items_ratio > ncw) return SMRE_OK;   // too many items per warp
-    const int threads = (ncw + 1) * 32;
-    const size_t xs_bytes = (size_t)stage_floats * 4;   // the largest band
     const size_t stage_offset = 512 + (seg_max + 127) / 128 * 128;
     const size_t budget = (size_t)smem_optin - 1024;   // static shared memory and slack
-    if (budget < stage_offset + xs_bytes) return SMRE_OK;
-    const long long fit = (long long)((budget - stage_offset - xs_bytes) / (stage_floats * 4));
-    const int S = (int)std::min<long long>(kMaxStages, fit);
-    if (S < 3) return SMRE_OK;
-    const size_t smem = stage_offset + (size_t)S * stage_floats * 4 + xs_bytes;
-    int occ = 0;
-    cudaError_t oe = persist_occupancy(sp, pitch, threads, smem, &occ);
-    if (oe != cudaSuccess || occ < 1) {
-        cudaGetLastError();
-        return SMRE_OK;
+    int ncw = 0, threads = 0, S = 0;
+    size_t smem = 0, reg_stage_offset = 0;
+    bool reg = false;
+    if (!(flags & SMRE_F_BAND_IN_SMEM) && persist_reg_fits(pitch, maxL, max_band)) {
+        // register-band kernel: warps of 64 columns, stages of packed rows,
+        // plus the column-sum exchange arrays
+        const int rncw = (pitch + 63) / 64;
+        const int rthreads = (rncw + 2) * 32;   // consumers, producer, storer
+        const size_t xb = persist_reg_exchange_bytes(pitch);
+        const size_t roff = kRegHeaderBytes + (seg_max + 127) / 128 * 128;
+        const long long fit = budget > roff + xb
+                                  ? (long long)((budget - roff - xb) / (stage_floats_reg * 4))
+                                  : 0;
+        const int rS = (int)std::min<long long>(kMaxStages, fit);
+        const size_t rsmem = roff + (size_t)rS * stage_floats_reg * 4 + xb;
+        int occ = 0;
+        if (rS >= 3) {
+            cudaError_t oe = persist_reg_occupancy(rthreads, rsmem, &occ);
+            if (oe != cudaSuccess) {
+                cudaGetLastError();
+                occ = 0;
+            }
+        }
+        if (occ >= 1) {
+            reg = true;
+            ncw = rncw;
+            threads = rthreads;
+            S = rS;
+            smem = rsmem;
+            stage_floats = stage_floats_reg;
+            reg_stage_offset = roff;
+        }
     }
+    if (!reg) {
+        ncw = std::max(4, std::min(kPersistThreads / 32 - 1, max_items));
+        if (items_ratio > ncw) return SMRE_OK;   // too many items per warp
+        threads = (ncw + 1) * 32;
+        const size_t xs_bytes = (size_t)stage_floats * 4;   // the largest band
+        if (budget < stage_offset + xs_bytes) return SMRE_OK;
+        const long long fit = (long long)((budget - stage_offset - xs_bytes) / (stage_floats * 4));
+        S = (int)std::min<long long>(kMaxStages, fit);
+        if (S < 3) return SMRE_OK;
+        smem = stage_offset + (size_t)S * stage_floats * 4 + xs_bytes;
+        int occ = 0;
+        cudaError_t oe = persist_occupancy(sp, pitch, threads, smem, &occ);
+        if (oe != cudaSuccess || occ < 1) {
+            cudaGetLastError();
+            return SMRE_OK;
+        }
+    }
+    // the register kernel keeps one flag per (event, consumer warp)
+    const int nflag_all = nflags * (reg ? ncw : 1);
 
     auto up = [&](auto **dptr, const auto &vec) -> cudaError_t {
         using E = typename std::remove_reference<decltype(vec[0])>::type;
@@ -662,19 +707,29 @@ smre_status plan_persistent(smre_dykstra *h, int flags)
     };
     CK(h, up(&h->d_sched, sched));
     CK(h, up(&h->d_cta_off, cta_off));
-    CK(h, cudaMalloc(&h->d_flags, sizeof(unsigned) * std::max(nflags, 1)));
+    CK(h, cudaMalloc(&h->d_flags, sizeof(unsigned) * std::max(nflag_all, 1)));
     CK(h, cudaMalloc(&h->d_barrier, 64));
     CK(h, cudaMalloc(&h->d_selftest, 64));
     CK(h, cudaMemset(h->d_selftest, 0, 64));
     CK(h, cudaMalloc(&h->d_abort, 64));
     CK(h, cudaMalloc(&h->d_ppartials, sizeof(double) * 4 * G));
     // zero source of the first cycle's copies (one unit-pass of rows at most)
-    const size_t zero_floats = (size_t)stage_floats / sp * pitch;
+    const size_t zero_floats = reg ? (size_t)stage_floats : (size_t)stage_floats / sp * pitch;
     CK(h, cudaMalloc(&h->d_zeros, sizeof(float) * zero_floats));
     CK(h, cudaMemset(h->d_zeros, 0, sizeof(float) * zero_floats));
-    h->dev_bytes += sizeof(unsigned) * nflags + 192 + sizeof(double) * 4 * G +
+    h->dev_bytes += sizeof(unsigned) * nflag_all + 192 + sizeof(double) * 4 * G +
                     sizeof(float) * zero_floats;
-    h->n_tasks = nflags;
+    h->n_tasks = nflag_all;
+    h->p_reg = reg;
+    if (reg) {
+        // rows handed over at offset transitions: one slot of pitch tagged
+        // words per event, zero (no valid tag) until first written
+        h->xch_words = (size_t)std::max(nflags, 1) * pitch;
+        const size_t xbytes = sizeof(unsigned long long) * h->xch_words;
+        CK(h, cudaMalloc(&h->d_xch, xbytes));
+        CK(h, cudaMemset(h->d_xch, 0, xbytes));
+        h->dev_bytes += xbytes;
+    }
     h->p_sp = sp;
     h->p_grid = G;
     h->p_threads = threads;
@@ -683,7 +738,7 @@ smre_status plan_persistent(smre_dykstra *h, int flags)
     h->p_maxL = maxL;
     h->p_smem = smem;
     h->p_stage_floats = (int)stage_floats;
-    h->p_stage_offset = (int)stage_offset;
+    h->p_stage_offset = (int)(reg ? reg_stage_offset : stage_offset);
     h->p_sched_bytes = (int)seg_max;
     if (const char *env = getenv("SMRE_WAIT_TIMEOUT_MS")) {
         const double ms = atof(env);
@@ -727,7 +782,19 @@ smre_status run_persistent(smre_dykstra *h)
     A.abort_word = h->d_abort;
     A.selftest_timeout = (h->flags & SMRE_F_SELFTEST_TIMEOUT) ? 1 : 0;
     A.selftest_flag = h->d_selftest;
-    CK(h, launch_persist(A, h->p_sp, h->p_grid, h->p_threads, h->p_smem, h->stream));
+    A.xch = h->d_xch;
+    // tags of this launch: tag_base + 1 .. tag_base + max_cycles, disjoint
+    // from the previous launches' (0 never occurs)
+    if ((unsigned long long)h->tag_next + (unsigned)h->max_cycles + 2ull > 0xffffffffull) {
+        CK(h, cudaMemsetAsync(h->d_xch, 0, sizeof(unsigned long long) * h->xch_words, h->stream));
+        h->tag_next = 1;
+    }
+    A.tag_base = h->tag_next;
+    h->tag_next += (unsigned)h->max_cycles + 1u;
+    if (h->p_reg)
+        CK(h, launch_persist_reg(A, h->p_grid, h->p_threads, h->p_smem, h->stream));
+    else
+        CK(h, launch_persist(A, h->p_sp, h->p_grid, h->p_threads, h->p_smem, h->stream));
     h->launches += 1;
     return SMRE_OK;
 }
@@ -1140,6 +1207,7 @@ void smre_dykstra_destroy(smre_dykstra *h)
     cudaFree(h->d_abort);
     cudaFree(h->d_ppartials);
     cudaFree(h->d_zeros);
+    cudaFree(h->d_xch);
     if (h->ctl_host) cudaFreeHost(h->ctl_host);
     if (h->viol_host) cudaFreeHost(h->viol_host);
     if (h->ev0) cudaEventDestroy(h->ev0);

@@ -112,6 +112,11 @@ struct PersistArgs {
     int *abort_word;
     int selftest_timeout;
     const unsigned *selftest_flag;
+    // register-band kernel only: rows handed to the upper neighbour at offset
+    // transitions, one slot of `pitch` 64-bit words (value | tag << 32) per
+    // event, and the tag base of this launch (tag = tag_base + cycle + 1)
+    unsigned long long *xch;
+    unsigned tag_base;
 };
 
 // ---- batched path (smre_batch.cu): many images, one launch per group step
@@ -203,6 +208,20 @@ smre_status batch_run_one(smre_batch *b, int height, int width, const float *x0,
 smre_status batch_submit_ld(smre_batch *b, int height, int width, const float *x0, int ld,
                             int *slot);
 smre_status batch_retrieve_ld(smre_batch *b, int slot, float *x, int ld, smre_result *res);
+
+// ---- persistent standard path, band in registers (smre_persist_reg.cu)
+constexpr int kRegRows = 8;                 // band rows a lane holds (largest side it takes)
+constexpr int kRegMaxWarps = 16;            // consumer warps of 64 columns: pitch <= 1024
+constexpr int kRegMaxThreads = (kRegMaxWarps + 2) * 32;   // consumers, producer, storer
+constexpr int kRegHeaderBytes = 1024;       // mbarriers and flags before the schedule table
+// the shape fits the register-band kernel: pitch <= 1024, sides <= 8, every
+// side task's band at most kRegRows rows
+bool persist_reg_fits(int pitch, int max_side, int max_band_rows);
+// shared memory of its column-sum exchange arrays
+size_t persist_reg_exchange_bytes(int pitch);
+cudaError_t persist_reg_occupancy(int threads, size_t smem, int *blocks_per_sm);
+cudaError_t launch_persist_reg(const PersistArgs &A, int grid, int threads, size_t smem,
+                               cudaStream_t s);
 
 bool persist_supported(int max_side);
 // shared-memory row stride (power of two >= pitch, 128..1024) or 0 if too wide
