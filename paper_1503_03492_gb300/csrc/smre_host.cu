@@ -82,6 +82,7 @@ struct smre_dykstra {
     double *d_ppartials = nullptr;
     float *d_zeros = nullptr;
     unsigned long long *d_xch = nullptr;   // register kernel: tagged transition rows
+    unsigned *d_smid = nullptr;            // register kernel: SM id of each CTA
     unsigned tag_next = 1;                 // tag base of the next persistent launch
     size_t xch_words = 0;
     int *d_abort = nullptr;
@@ -708,7 +709,7 @@ smre_status plan_persistent(smre_dykstra *h, int flags)
     CK(h, up(&h->d_sched, sched));
     CK(h, up(&h->d_cta_off, cta_off));
     CK(h, cudaMalloc(&h->d_flags, sizeof(unsigned) * std::max(nflag_all, 1)));
-    CK(h, cudaMalloc(&h->d_barrier, 64));
+    CK(h, cudaMalloc(&h->d_barrier, 128));   // [0]: per-cycle grid barrier, [16]: launch prologue
     CK(h, cudaMalloc(&h->d_selftest, 64));
     CK(h, cudaMemset(h->d_selftest, 0, 64));
     CK(h, cudaMalloc(&h->d_abort, 64));
@@ -728,7 +729,8 @@ smre_status plan_persistent(smre_dykstra *h, int flags)
         const size_t xbytes = sizeof(unsigned long long) * h->xch_words;
         CK(h, cudaMalloc(&h->d_xch, xbytes));
         CK(h, cudaMemset(h->d_xch, 0, xbytes));
-        h->dev_bytes += xbytes;
+        CK(h, cudaMalloc(&h->d_smid, sizeof(unsigned) * G));
+        h->dev_bytes += xbytes + sizeof(unsigned) * G;
     }
     h->p_sp = sp;
     h->p_grid = G;
@@ -752,7 +754,7 @@ smre_status plan_persistent(smre_dykstra *h, int flags)
 smre_status run_persistent(smre_dykstra *h)
 {
     CK(h, cudaMemsetAsync(h->d_flags, 0, sizeof(unsigned) * std::max(h->n_tasks, 1), h->stream));
-    CK(h, cudaMemsetAsync(h->d_barrier, 0, 64, h->stream));
+    CK(h, cudaMemsetAsync(h->d_barrier, 0, 128, h->stream));
     CK(h, cudaMemsetAsync(h->d_abort, 0, 64, h->stream));
     PersistArgs A{};
     A.x = h->xw;
@@ -783,6 +785,7 @@ smre_status run_persistent(smre_dykstra *h)
     A.selftest_timeout = (h->flags & SMRE_F_SELFTEST_TIMEOUT) ? 1 : 0;
     A.selftest_flag = h->d_selftest;
     A.xch = h->d_xch;
+    A.smid_tab = h->d_smid;
     // tags of this launch: tag_base + 1 .. tag_base + max_cycles, disjoint
     // from the previous launches' (0 never occurs)
     if ((unsigned long long)h->tag_next + (unsigned)h->max_cycles + 2ull > 0xffffffffull) {
@@ -1208,6 +1211,7 @@ void smre_dykstra_destroy(smre_dykstra *h)
     cudaFree(h->d_ppartials);
     cudaFree(h->d_zeros);
     cudaFree(h->d_xch);
+    cudaFree(h->d_smid);
     if (h->ctl_host) cudaFreeHost(h->ctl_host);
     if (h->viol_host) cudaFreeHost(h->viol_host);
     if (h->ev0) cudaEventDestroy(h->ev0);

@@ -117,6 +117,7 @@ struct PersistArgs {
     // event, and the tag base of this launch (tag = tag_base + cycle + 1)
     unsigned long long *xch;
     unsigned tag_base;
+    unsigned *smid_tab;          // [G] SM id of each CTA (the launch orders bands by it)
 };
 
 // ---- batched path (smre_batch.cu): many images, one launch per group step

@@ -291,9 +291,19 @@ struct RegCtx {
     unsigned cs32, cs64;        // shared addresses of the column-sum arrays
     unsigned cs_half;           // bytes of one FP32 column-sum buffer
     unsigned *near_tag;         // [warps] last near-window tag each warp published
+    volatile int *abort_cta;    // set (never cleared) when a warp of the CTA lost a wait
     int S, NC, warp, lane, pitch, W, c0;
     bool lane_ok;               // c0 < pitch
 };
+
+// Pass barrier of the consumer warps; returns true when any of them lost a
+// wait (a sticky shared flag, written before the barrier and read after it).
+__device__ __forceinline__ bool pass_barrier(const RegCtx &cx, bool bad)
+{
+    if (bad && cx.lane == 0) *cx.abort_cta = 1;
+    named_sync(1, cx.NC);
+    return *cx.abort_cta != 0;
+}
 
 // Side 1: every window is one pixel, so the pass needs no exchange and no
 // barrier.  A wait this warp missed stays in `lost` until the next OR-barrier.
@@ -378,19 +388,18 @@ __device__ __forceinline__ bool reg_task(const RegCtx &cx, const RegTask &ts,
         const bool in1 = work && p0 + 1 >= 0 && p0 + 1 < nvL;
         const int s0 = in0 ? c0 - p0 % L : 0;          // first column of each column's window
         const int s1 = in1 ? c0 + 1 - (p0 + 1) % L : 0;
-        float2 y[kRegRows];
+        // y = x + q replaces x in the registers: columns outside every window
+        // of the pass have q = 0 there (each cycle stores y - y * 1 = 0 for
+        // them, the first cycle reads zeros), so y * 1 gives their x back
         if (work) {
 #pragma unroll
             for (int u = 0; u < UM; ++u) {
                 if (u < U) {
-                    float2 q2[L];
-#pragma unroll
-                    for (int i = 0; i < L; ++i) q2[i] = lds2(stg + (unsigned)(u * L + i) * rowb);
                     float2 cs = make_float2(0.f, 0.f);
 #pragma unroll
                     for (int i = 0; i < L; ++i) {
-                        y[u * L + i] = __fadd2_rn(xr[u * L + i], q2[i]);
-                        cs = __ffma2_rn(y[u * L + i], y[u * L + i], cs);
+                        xr[u * L + i] = __fadd2_rn(xr[u * L + i], lds2(stg + (unsigned)(u * L + i) * rowb));
+                        cs = __ffma2_rn(xr[u * L + i], xr[u * L + i], cs);
                     }
                     sts2(csb + (unsigned)u * rowb + (unsigned)c0 * 4u, cs);
                 }
@@ -398,21 +407,36 @@ __device__ __forceinline__ bool reg_task(const RegCtx &cx, const RegTask &ts,
         }
         // every column sum of the pass is in shared memory; a copy lost
         // anywhere in the CTA abandons the launch here
-        if (named_sync_or(1, bad, cx.NC)) return true;
+        if (pass_barrier(cx, bad)) return true;
+        // Each lane adds the column sums of the window of its first column.
+        // The window of the second column is the same one, or it starts at
+        // that column and then also holds the next lane's first column, whose
+        // sum the next lane formed in the same order; only lane 31 forms it
+        // itself (its next lane is in the next warp), when a window starts at
+        // column 64 w + 63.
+        const int c31 = 64 * cx.warp + 63 - b;
+        const bool own31 = c31 >= 0 && c31 < nvL && c31 % L == 0;
 #pragma unroll
         for (int u = 0; u < UM; ++u) {
             if (u < U) {
                 const unsigned rb = csb + (unsigned)u * rowb;
-                float v0[L], v1[L];
+                float v0[L];
 #pragma unroll
                 for (int m = 0; m < L; ++m) v0[m] = lds1(rb + (unsigned)(s0 + m) * 4u);
+                float t0 = v0[0];
 #pragma unroll
-                for (int m = 0; m < L; ++m) v1[m] = lds1(rb + (unsigned)(s1 + m) * 4u);
-                float t0 = v0[0], t1 = v1[0];
+                for (int m = 1; m < L; ++m) t0 += v0[m];
+                const float tn = __shfl_down_sync(kFull, t0, 1);
+                float t1 = (in0 && s1 == s0) ? t0 : tn;
+                if (own31) {
+                    // warp-uniform: only lane 31's value is kept
+                    float v1[L];
 #pragma unroll
-                for (int m = 1; m < L; ++m) {
-                    t0 += v0[m];
-                    t1 += v1[m];
+                    for (int m = 0; m < L; ++m) v1[m] = lds1(rb + (unsigned)(s1 + m) * 4u);
+                    float t31 = v1[0];
+#pragma unroll
+                    for (int m = 1; m < L; ++m) t31 += v1[m];
+                    if (cx.lane == 31) t1 = t31;
                 }
                 float sc0 = 1.f, sc1 = 1.f;
                 const bool nr0 = in0 && fabsf(t0 - cS) <= kNearBand * cS;
@@ -424,8 +448,8 @@ __device__ __forceinline__ bool reg_task(const RegCtx &cx, const RegTask &ts,
                     if (work) {
 #pragma unroll
                         for (int i = 0; i < L; ++i) {
-                            c64x = fma((double)y[u * L + i].x, (double)y[u * L + i].x, c64x);
-                            c64y = fma((double)y[u * L + i].y, (double)y[u * L + i].y, c64y);
+                            c64x = fma((double)xr[u * L + i].x, (double)xr[u * L + i].x, c64x);
+                            c64y = fma((double)xr[u * L + i].y, (double)xr[u * L + i].y, c64y);
                         }
                     }
                     const float3 r = near_scales<L>(
@@ -437,16 +461,15 @@ __device__ __forceinline__ bool reg_task(const RegCtx &cx, const RegTask &ts,
                     sc1 = r.y;
                     if (r.z == 0.f) lost = true;
                 }
-                // x = y * scale stays in the registers; q = y - x over the
-                // stage (the storer warp copies it to the plane)
+                // x = y * scale stays in the registers (scale 1 outside the
+                // windows); q = y - x over the stage (copied to the plane)
                 if (work) {
                     const float2 sc = make_float2(sc0, sc1);
 #pragma unroll
                     for (int i = 0; i < L; ++i) {
-                        const float2 yv = y[u * L + i];
+                        const float2 yv = xr[u * L + i];
                         const float2 xn = __fmul2_rn(yv, sc);
-                        if (in0) xr[u * L + i].x = xn.x;
-                        if (in1) xr[u * L + i].y = xn.y;
+                        xr[u * L + i] = xn;
                         sts2(stg + (unsigned)(u * L + i) * rowb, __fadd2_rn(yv, make_float2(-xn.x, -xn.y)));
                     }
                 }
@@ -460,19 +483,6 @@ __device__ __forceinline__ bool reg_task(const RegCtx &cx, const RegTask &ts,
         lost = lost || bad;
     }
     return false;
-}
-
-__device__ __forceinline__ bool run_reg_task(const RegCtx &cx, int L, const RegTask &ts,
-                                             float2 (&xr)[kRegRows], int &s_cur, unsigned &fph,
-                                             unsigned &ptag, bool &lost)
-{
-    switch (L) {
-#define RT(l) case l: return reg_task<l>(cx, ts, xr, s_cur, fph, ptag, lost);
-        case 1: reg_task1(cx, ts, xr, s_cur, fph, ptag, lost); return false;
-        RT(2) RT(3) RT(4) RT(5) RT(6) RT(7) RT(8)
-#undef RT
-        default: return true;
-    }
 }
 
 // Row r of the band (runtime index) as a register select.
@@ -515,6 +525,95 @@ __device__ __forceinline__ void publish_rows(const PersistArgs &A, const float2 
             }
         }
     }
+}
+
+// What a consumer warp carries from one side to the next within a cycle.
+struct CycState {
+    double d2, n2;     // this thread's share of the cycle norm
+    int s_cur;         // stage of the next pass
+    unsigned fph;      // parity of the next `full` wait, per stage
+    unsigned ptag;     // passes run so far (column-sum buffer parity, near tags)
+    bool lost;         // this warp missed a wait
+};
+
+// Every offset a of one side for one consumer warp, after the side-start
+// wait: the band comes in, slides down one row per offset (the top row goes
+// to the upper neighbour, the lower neighbour's comes in), the passes of each
+// offset run, and the band is stored at the end.  Returns true when the CTA
+// must abandon the launch.  Side L is known at compile time, and the band's
+// registers live only here.
+template <int L>
+__device__ __forceinline__ bool run_side(const RegCtx &cx, const SideS &sd, const GrpS *grps_s,
+                                         unsigned want, unsigned tag, CycState &cs)
+{
+    const PersistArgs &A = *cx.A;
+    const int band = sd.U * L, pitch = cx.pitch, c0 = cx.c0;
+    const bool lane_ok = cx.lane_ok;
+    float2 xr[kRegRows];
+#pragma unroll
+    for (int k = 0; k < kRegRows; ++k) xr[k] = make_float2(0.f, 0.f);
+    if (!cs.lost && lane_ok) {
+#pragma unroll
+        for (int k = 0; k < kRegRows; ++k)
+            if (k < band && sd.r0 + k < A.H) xr[k] = ldcg2(A.x + (size_t)(sd.r0 + k) * pitch + c0);
+    }
+    for (int a = 0; a < L; ++a) {
+        const GrpS gp = grps_s[sd.grp0 + a];
+        if (a > 0) {
+            // the band slides down one row: drop the (published) top row,
+            // take the lower neighbour warp's top row of offset a-1
+#pragma unroll
+            for (int k = 0; k + 1 < kRegRows; ++k)
+                if (k + 1 < band) xr[k] = xr[k + 1];
+            const int r = sd.r0 + a - 1 + band;
+            if (!cs.lost && r < A.H) {
+                float2 v = make_float2(0.f, 0.f);
+                if (gp.nb_flag >= 0) {
+                    const float3 t = take_tagged(A, A.xch + (size_t)gp.nb_flag * pitch + c0, tag, lane_ok);
+                    v = make_float2(t.x, t.y);
+                    if (t.z == 0.f) cs.lost = true;
+                } else if (lane_ok) {
+                    v = ldcg2(A.x + (size_t)r * pitch + c0);   // no task of this side wrote it
+                }
+                set_row(xr, band - 1, v);
+            }
+        }
+        if (gp.U > 0) {
+            const RegTask rt{gp.U, sd.pass0 + a * L, sd.cS, sd.sqrt_cS, sd.cS64};
+            bool ab;
+            if (L == 1) {
+                reg_task1(cx, rt, xr, cs.s_cur, cs.fph, cs.ptag, cs.lost);
+                ab = false;
+            } else {
+                ab = reg_task<L == 1 ? 2 : L>(cx, rt, xr, cs.s_cur, cs.fph, cs.ptag, cs.lost);
+            }
+            if (ab) return true;
+        }
+        if (cs.lost) continue;
+        if (a < L - 1) {
+            // the top row leaves the band: to the image, and tagged to the
+            // upper neighbour, which takes it at offset a + 1
+            publish_rows(A, xr, sd.r0 + a, 1, (unsigned long long)((sd.top_final >> a) & 1u), c0,
+                         lane_ok, cs.d2, cs.n2);
+            if (lane_ok) {
+                const unsigned long long tg = (unsigned long long)tag << 32;
+                st_relaxed_v2(A.xch + (size_t)(sd.flag0 + a) * pitch + c0,
+                              tg | __float_as_uint(xr[0].x), tg | __float_as_uint(xr[0].y));
+            }
+        } else {
+            // side end: the whole band to the image, then the flags of every
+            // event of the side (later sides wait on them)
+            publish_rows(A, xr, sd.r0 + a, band, sd.end_final, c0, lane_ok, cs.d2, cs.n2);
+            __syncwarp();
+            if (cx.lane == 0) {
+                __threadfence();
+                const int NCW = A.consumer_warps;
+                for (int e = 0; e < L; ++e)
+                    st_relaxed_u32(A.flags + (size_t)(sd.flag0 + e) * NCW + cx.warp, want);
+            }
+        }
+    }
+    return false;
 }
 
 enum { kGo = 0, kStop = 1, kAbort = 2 };
@@ -578,13 +677,37 @@ __global__ void __launch_bounds__((NW + 2) * 32, 1) persist_reg_kernel(const __g
     float *cs32 = stage0 + (size_t)S * A.stage_floats;                // [2][kRegRows/2][pitch]
     double *cs64 = reinterpret_cast<double *>(cs32 + (size_t)kRegRows * A.pitch);
     __shared__ int s_dec;
+    __shared__ int s_abort;
     __shared__ double s_red[2][32];
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
     const int NCW = A.consumer_warps, NC = NCW * 32;
-    const int cta = blockIdx.x, G = gridDim.x;
+    const int G = gridDim.x;
     const int pitch = A.pitch;
+    __shared__ int s_cta;
+
+    // Schedule index of this CTA: its rank among the SM ids of the launch
+    // (one CTA per SM), so that neighbouring bands -- which hand rows to each
+    // other at every offset -- run on SMs with neighbouring ids.
+    if (tid == 0) {
+        unsigned smid;
+        asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+        int rank = (int)blockIdx.x;
+        A.smid_tab[blockIdx.x] = smid;
+        __threadfence();
+        atomicAdd(A.barrier + 16, 1u);
+        if (wait_geq(A, A.barrier + 16, (unsigned)G)) {
+            rank = 0;
+            for (int i = 0; i < G; ++i) {
+                const unsigned o = __ldcg(A.smid_tab + i);
+                rank += o < smid || (o == smid && i < (int)blockIdx.x);
+            }
+        }
+        s_cta = rank;
+    }
+    __syncthreads();
+    const int cta = s_cta;
 
     {
         const int *hdr = reinterpret_cast<const int *>(A.sched + A.cta_off[cta]);
@@ -618,6 +741,7 @@ __global__ void __launch_bounds__((NW + 2) * 32, 1) persist_reg_kernel(const __g
         }
         fence_mbar_init();
         s_dec = kGo;
+        s_abort = 0;
     }
     __syncthreads();
 
@@ -737,90 +861,35 @@ __global__ void __launch_bounds__((NW + 2) * 32, 1) persist_reg_kernel(const __g
                     smem_u32(cs64),
                     (unsigned)(kRegRows / 2) * (unsigned)pitch * 4u,
                     near_tag,
+                    &s_abort,
                     S, NC, warp, lane, pitch, A.W, c0, lane_ok};
-    float2 xr[kRegRows];
-#pragma unroll
-    for (int k = 0; k < kRegRows; ++k) xr[k] = make_float2(0.f, 0.f);
-    int s_cur = 0;
-    unsigned fph = 0, ptag = 0;
-    double d2 = 0.0, n2 = 0.0;
-    bool aborted = false, lost = false;
+    CycState cs{0.0, 0.0, 0, 0u, 0u, false};
+    bool aborted = false;
+    bool &lost = cs.lost;
 
     for (int cyc = 0;; ++cyc) {
         const unsigned want = (unsigned)(cyc + 1);
         const unsigned tag = A.tag_base + want;
         for (int si = 0; si < nside && !aborted; ++si) {
             const SideS &sd = sides_s[si];
-            const int L = sd.L, band = sd.U * L;
-
-            // side start: this warp's columns of the band, after the flags of
-            // the same warp of the last publishers of those rows
+            // side start: wait for the same warp of the last publishers of the
+            // band's rows (or a self-test flag nothing sets)
             if (lane == 0 && !lost) {
                 bool ok = true;
                 if (A.selftest_timeout && cta == 0 && si == 0 && warp == 0)
-                    ok = wait_geq(A, A.selftest_flag, 1u);   // a flag nothing sets
+                    ok = wait_geq(A, A.selftest_flag, 1u);
                 for (int k = 0; k < sd.dep_count && ok; ++k)
                     ok = wait_geq(A, A.flags + (size_t)deps_s[sd.dep_begin + k] * NCW + warp, want);
                 lost = !ok;
             }
             lost = __shfl_sync(kFull, lost ? 1 : 0, 0) != 0;
             __syncwarp();
-            if (!lost && lane_ok) {
-#pragma unroll
-                for (int k = 0; k < kRegRows; ++k)
-                    if (k < band && sd.r0 + k < A.H) xr[k] = ldcg2(A.x + (size_t)(sd.r0 + k) * pitch + c0);
-            }
-
-            for (int a = 0; a < L; ++a) {
-                const GrpS gp = grps_s[sd.grp0 + a];
-                if (a > 0) {
-                    // the band slides down one row: drop the (published) top
-                    // row, take the lower neighbour warp's top row of offset a-1
-#pragma unroll
-                    for (int k = 0; k + 1 < kRegRows; ++k)
-                        if (k + 1 < band) xr[k] = xr[k + 1];
-                    const int r = sd.r0 + a - 1 + band;
-                    if (!lost && r < A.H) {
-                        float2 v = make_float2(0.f, 0.f);
-                        if (gp.nb_flag >= 0) {
-                            const float3 t = take_tagged(A, A.xch + (size_t)gp.nb_flag * pitch + c0, tag, lane_ok);
-                            v = make_float2(t.x, t.y);
-                            if (t.z == 0.f) lost = true;
-                        } else if (lane_ok) {
-                            v = ldcg2(A.x + (size_t)r * pitch + c0);   // no task of this side wrote it
-                        }
-                        set_row(xr, band - 1, v);
-                    }
-                }
-                if (gp.U > 0) {
-                    const RegTask rt{gp.U, sd.pass0 + a * L, sd.cS, sd.sqrt_cS, sd.cS64};
-                    if (run_reg_task(cx, L, rt, xr, s_cur, fph, ptag, lost)) {
-                        aborted = true;
-                        break;
-                    }
-                }
-                if (lost) continue;
-                if (a < L - 1) {
-                    // the top row leaves the band: to the image, and tagged to
-                    // the upper neighbour, which takes it at offset a + 1
-                    publish_rows(A, xr, sd.r0 + a, 1, (unsigned long long)((sd.top_final >> a) & 1u),
-                                 c0, lane_ok, d2, n2);
-                    if (lane_ok) {
-                        const unsigned long long tg = (unsigned long long)tag << 32;
-                        st_relaxed_v2(A.xch + (size_t)(sd.flag0 + a) * pitch + c0,
-                                      tg | __float_as_uint(xr[0].x), tg | __float_as_uint(xr[0].y));
-                    }
-                } else {
-                    // side end: the whole band to the image, then the flags of
-                    // every event of the side (later sides wait on them)
-                    publish_rows(A, xr, sd.r0 + a, band, sd.end_final, c0, lane_ok, d2, n2);
-                    __syncwarp();
-                    if (lane == 0) {
-                        __threadfence();
-                        for (int e = 0; e < L; ++e)
-                            st_relaxed_u32(A.flags + (size_t)(sd.flag0 + e) * NCW + warp, want);
-                    }
-                }
+            // one dispatch per side: the band lives inside the side's own code
+            switch (sd.L) {
+#define RS(l) case l: aborted = run_side<l>(cx, sd, grps_s, want, tag, cs); break;
+                RS(1) RS(2) RS(3) RS(4) RS(5) RS(6) RS(7) RS(8)
+#undef RS
+                default: aborted = true; break;
             }
         }
 
@@ -828,7 +897,7 @@ __global__ void __launch_bounds__((NW + 2) * 32, 1) persist_reg_kernel(const __g
         int dec = kGo;
         if (!aborted) {
             double *slot = A.partials + (size_t)(cyc & 1) * 2 * G;   // double-buffered
-            double sa = d2, sb = n2;
+            double sa = cs.d2, sb = cs.n2;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 sa += __shfl_xor_sync(kFull, sa, o);
@@ -854,8 +923,8 @@ __global__ void __launch_bounds__((NW + 2) * 32, 1) persist_reg_kernel(const __g
                 late = !wait_geq(A, A.barrier, (unsigned)G * want);
             }
             if (!aborted) late = named_sync_or(1, late, NC);
-            d2 = 0.0;
-            n2 = 0.0;
+            cs.d2 = 0.0;
+            cs.n2 = 0.0;
             if (aborted || late) {
                 aborted = true;
             } else {
