@@ -305,8 +305,25 @@ __device__ __forceinline__ bool pass_barrier(const RegCtx &cx, bool bad)
     return *cx.abort_cta != 0;
 }
 
+// Side 1, rare path: the FP64 ball test of single-pixel windows near the
+// boundary.  Out of line, so that none of its FP64 work is scheduled on the
+// common path (FP64 runs at a small fraction of the FP32 rate on this part).
+__device__ __noinline__ float2 near_scales1(float2 y, bool nr0, bool nr1, double cS64, float sc0,
+                                            float sc1)
+{
+    if (nr0) {
+        const double t64 = fma((double)y.x, (double)y.x, 0.0);
+        sc0 = t64 > cS64 ? (float)sqrt(cS64 / t64) : 1.f;
+    }
+    if (nr1) {
+        const double t64 = fma((double)y.y, (double)y.y, 0.0);
+        sc1 = t64 > cS64 ? (float)sqrt(cS64 / t64) : 1.f;
+    }
+    return make_float2(sc0, sc1);
+}
+
 // Side 1: every window is one pixel, so the pass needs no exchange and no
-// barrier.  A wait this warp missed stays in `lost` until the next OR-barrier.
+// barrier.  A wait this warp missed stays in `lost` until the next barrier.
 __device__ __forceinline__ void reg_task1(const RegCtx &cx, const RegTask &ts,
                                           float2 (&xr)[kRegRows], int &s_cur, unsigned &fph,
                                           unsigned &ptag, bool &lost)
@@ -324,24 +341,24 @@ __device__ __forceinline__ void reg_task1(const RegCtx &cx, const RegTask &ts,
     const bool work = !bad && cx.lane_ok;
     const bool in0 = work && c0 < cx.W;
     const bool in1 = work && c0 + 1 < cx.W;
-    if (work) {
 #pragma unroll
-        for (int u = 0; u < kRegRows; ++u) {
-            if (u < U) {
-                const float2 y = __fadd2_rn(xr[u], lds2(stg + (unsigned)u * rowb));
-                // window sum: 0 + y^2 rounded once, as in every schedule
-                const float2 t = __ffma2_rn(y, y, make_float2(0.f, 0.f));
-                float sc0 = 1.f, sc1 = 1.f;
-                if (in0 && t.x > cS) sc0 = sqrt_cS * rsqrtf(t.x);
-                if (in1 && t.y > cS) sc1 = sqrt_cS * rsqrtf(t.y);
-                if (in0 && fabsf(t.x - cS) <= kNearBand * cS) {
-                    const double t64 = fma((double)y.x, (double)y.x, 0.0);
-                    sc0 = t64 > ts.cS64 ? (float)sqrt(ts.cS64 / t64) : 1.f;
-                }
-                if (in1 && fabsf(t.y - cS) <= kNearBand * cS) {
-                    const double t64 = fma((double)y.y, (double)y.y, 0.0);
-                    sc1 = t64 > ts.cS64 ? (float)sqrt(ts.cS64 / t64) : 1.f;
-                }
+    for (int u = 0; u < kRegRows; ++u) {
+        if (u < U) {
+            float2 y = xr[u];
+            if (work) y = __fadd2_rn(y, lds2(stg + (unsigned)u * rowb));
+            // window sum: 0 + y^2 rounded once, as in every schedule
+            const float2 t = __ffma2_rn(y, y, make_float2(0.f, 0.f));
+            float sc0 = 1.f, sc1 = 1.f;
+            if (in0 && t.x > cS) sc0 = sqrt_cS * rsqrtf(t.x);
+            if (in1 && t.y > cS) sc1 = sqrt_cS * rsqrtf(t.y);
+            const bool nr0 = in0 && fabsf(t.x - cS) <= kNearBand * cS;
+            const bool nr1 = in1 && fabsf(t.y - cS) <= kNearBand * cS;
+            if (__any_sync(kFull, nr0 || nr1)) {
+                const float2 r = near_scales1(y, nr0, nr1, ts.cS64, sc0, sc1);
+                sc0 = r.x;
+                sc1 = r.y;
+            }
+            if (work) {
                 const float2 xn = __fmul2_rn(y, make_float2(sc0, sc1));
                 if (in0) xr[u].x = xn.x;
                 if (in1) xr[u].y = xn.y;
@@ -493,12 +510,31 @@ __device__ __forceinline__ void set_row(float2 (&xr)[kRegRows], int r, float2 v)
         if (k == r) xr[k] = v;
 }
 
+// x_prev of the rows that a publication of band rows 0 .. n-1 (image rows
+// r_first ..) makes final in the cycle, loaded ahead of the passes that end
+// in that publication (bit k of `fin`: band row k is final).
+template <int PF>
+__device__ __forceinline__ void prefetch_prev(const PersistArgs &A, float2 (&pv)[PF], int r_first,
+                                              int n, unsigned long long fin, int c0, bool lane_ok)
+{
+    if (!lane_ok || !fin) return;
+#pragma unroll
+    for (int k = 0; k < PF; ++k) {
+        const int r = r_first + k;
+        if (k < n && r < A.H && ((fin >> k) & 1ull))
+            pv[k] = __ldcg(reinterpret_cast<const float2 *>(A.xprev + (size_t)r * A.pitch + c0));
+    }
+}
+
 // Store band rows 0 .. n-1 to image rows r_first ..; rows whose bit is set in
 // `fin` are final in the cycle: add their step and previous norm (FP64) and
-// keep them as the next cycle's x_prev.
+// keep them as the next cycle's x_prev (taken from pv where PF covers the
+// row, else loaded here).
+template <int PF, bool USE_PV>
 __device__ __forceinline__ void publish_rows(const PersistArgs &A, const float2 (&xr)[kRegRows],
-                                             int r_first, int n, unsigned long long fin, int c0,
-                                             bool lane_ok, double &d2, double &n2)
+                                             const float2 (&pv)[PF], int r_first, int n,
+                                             unsigned long long fin, int c0, bool lane_ok,
+                                             double &d2, double &n2)
 {
     if (!lane_ok) return;
     const int pitch = A.pitch;
@@ -510,16 +546,16 @@ __device__ __forceinline__ void publish_rows(const PersistArgs &A, const float2 
             *reinterpret_cast<float2 *>(A.x + (size_t)r * pitch + c0) = v;
             if ((fin >> k) & 1ull) {
                 float2 *pp = reinterpret_cast<float2 *>(A.xprev + (size_t)r * pitch + c0);
-                const float2 pv = __ldcg(pp);
+                const float2 pv_k = USE_PV && k < PF ? pv[k < PF ? k : 0] : __ldcg(pp);
                 if (c0 < A.W) {
-                    const double dd = (double)v.x - (double)pv.x;
+                    const double dd = (double)v.x - (double)pv_k.x;
                     d2 = fma(dd, dd, d2);
-                    n2 = fma((double)pv.x, (double)pv.x, n2);
+                    n2 = fma((double)pv_k.x, (double)pv_k.x, n2);
                 }
                 if (c0 + 1 < A.W) {
-                    const double dd = (double)v.y - (double)pv.y;
+                    const double dd = (double)v.y - (double)pv_k.y;
                     d2 = fma(dd, dd, d2);
-                    n2 = fma((double)pv.y, (double)pv.y, n2);
+                    n2 = fma((double)pv_k.y, (double)pv_k.y, n2);
                 }
                 *pp = v;
             }
@@ -578,6 +614,15 @@ __device__ __forceinline__ bool run_side(const RegCtx &cx, const SideS &sd, cons
                 set_row(xr, band - 1, v);
             }
         }
+        // x_prev of the rows this offset's publication makes final: loaded
+        // now, used after the passes (side 1 only: it is the last side of a
+        // cycle whenever the scale set holds it, and then every row becomes
+        // final there)
+        constexpr int PF = L == 1 ? kRegRows : 1;
+        float2 pv[PF];
+        const unsigned long long fin = a < L - 1 ? (unsigned long long)((sd.top_final >> a) & 1u)
+                                                 : sd.end_final;
+        if (L == 1 && !cs.lost) prefetch_prev<PF>(A, pv, sd.r0 + a, a < L - 1 ? 1 : band, fin, c0, lane_ok);
         if (gp.U > 0) {
             const RegTask rt{gp.U, sd.pass0 + a * L, sd.cS, sd.sqrt_cS, sd.cS64};
             bool ab;
@@ -593,8 +638,7 @@ __device__ __forceinline__ bool run_side(const RegCtx &cx, const SideS &sd, cons
         if (a < L - 1) {
             // the top row leaves the band: to the image, and tagged to the
             // upper neighbour, which takes it at offset a + 1
-            publish_rows(A, xr, sd.r0 + a, 1, (unsigned long long)((sd.top_final >> a) & 1u), c0,
-                         lane_ok, cs.d2, cs.n2);
+            publish_rows<PF, (L == 1)>(A, xr, pv, sd.r0 + a, 1, fin, c0, lane_ok, cs.d2, cs.n2);
             if (lane_ok) {
                 const unsigned long long tg = (unsigned long long)tag << 32;
                 st_relaxed_v2(A.xch + (size_t)(sd.flag0 + a) * pitch + c0,
@@ -603,7 +647,7 @@ __device__ __forceinline__ bool run_side(const RegCtx &cx, const SideS &sd, cons
         } else {
             // side end: the whole band to the image, then the flags of every
             // event of the side (later sides wait on them)
-            publish_rows(A, xr, sd.r0 + a, band, sd.end_final, c0, lane_ok, cs.d2, cs.n2);
+            publish_rows<PF, (L == 1)>(A, xr, pv, sd.r0 + a, band, fin, c0, lane_ok, cs.d2, cs.n2);
             __syncwarp();
             if (cx.lane == 0) {
                 __threadfence();
