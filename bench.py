@@ -145,11 +145,23 @@ class Clocks:
 
 
 # DRAM traffic of the dominant kernel from one ncu capture (20 cycles of this
-# workload, profiles/persist_kernel_emitters512_20cycles_full.md), per library
-# version: (first-cycle bytes, bytes per later cycle).  A version without an
-# entry reports traffic as null until it is captured again.
+# workload, profiles/persist_reg_kernel_emitters512_20cycles.md), per library
+# version: (first-cycle bytes, bytes per later cycle), the capture's total
+# split like the algorithmic bytes.  A version without an entry reports
+# traffic as null until it is captured again.
 MEASURED_TRAFFIC = {
-    "smre-gb300 0.7 (sm_103a)": (209.3e6, 416.5e6),
+    "smre-gb300 0.8 (sm_103a)": (217.6e6, 433.1e6),
+}
+
+# Warp instructions one incomplete projection of this workload executes
+# (icd_pass_kernel, passes i = 0..3, from one ncu capture:
+# profiles/icd_pass_kernel_emitters512_K3.md), per library version.  The
+# incomplete method is bound on chip (per-tile sweep chains in registers and
+# shuffles, about 8 B of HBM traffic per pixel and pass): its roofline is the
+# issue-slot ceiling, windows per second if every SM issued four warp
+# instructions per cycle at the measured clock.
+ICD_WARP_INSTRUCTIONS = {
+    "smre-gb300 0.8 (sm_103a)": 21737554,
 }
 
 
@@ -540,7 +552,7 @@ def main():
     launches0 = P.kernel_launches()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
-    std_s, std_bytes, std_windows, icd_windows, cycles = [], [], 0, 0, []
+    std_s, std_bytes, std_windows, icd_windows, cycles, icd_s = [], [], 0, 0, [], []
     with Clocks(lrank) as clk:
         torch.cuda.synchronize()
         for i in range(args.steps):
@@ -554,6 +566,7 @@ def main():
                              (r1.cycles - 1) * algorithmic_bytes_per_cycle(False))
             std_windows += r1.windows
             icd_windows += r2.windows
+            icd_s.append(r2.seconds)
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
@@ -586,6 +599,21 @@ def main():
     tr = MEASURED_TRAFFIC.get(smre.smre_version())
     cyc_med = int(np.median(cycles))
     traffic = None if tr is None else tr[0] + (cyc_med - 1) * tr[1]
+    # the incomplete projection against its on-chip (issue-slot) ceiling
+    icd_sec = sum(icd_s) / len(icd_s)
+    icd_w = icd_windows / args.steps
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    clk_mhz = clocks.get("sm_mhz") or 2070.0
+    ins = ICD_WARP_INSTRUCTIONS.get(smre.smre_version())
+    icd_ceiling = None if ins is None else icd_w / (ins / (n_sm * 4 * clk_mhz * 1e6))
+    roofline_icd = {"bound": "issue", "achieved": icd_w / icd_sec, "peak": icd_ceiling,
+                    "unit": "window-projections/s",
+                    "frac": None if icd_ceiling is None else (icd_w / icd_sec) / icd_ceiling,
+                    "kernel": "icd_pass_kernel<3> (passes i = 0..3 of one incomplete projection)",
+                    "peak_source": "warp instructions per call from ncu x (SMs x 4 issue slots x "
+                                   "median SM clock)",
+                    "warp_instructions_per_call": ins, "seconds_per_call": icd_sec,
+                    "hbm_bytes_per_call": 8 * H * W * (ICD_K + 1)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -619,10 +647,11 @@ def main():
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "persist_kernel (one launch = one standard projection)",
+                         "kernel": "persist_reg_kernel<8> (one launch = one standard projection)",
                          "peak_source": peak_src,
                          "bytes_per_launch": sum(std_bytes) / len(std_bytes),
                          "seconds_per_launch": avg_std},
+            "roofline_icd": roofline_icd,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": "window-projections/s",
                     "h2d_bytes_per_step": 2 * H * W * 4, "d2h_bytes_per_step": 2 * H * W * 4},

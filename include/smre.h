@@ -104,7 +104,8 @@ typedef enum {
 typedef struct {
     int height, width;          /* pixels: 1 <= height <= 65535, 1 <= width <= 4096 */
     const int *sides;           /* n_sides window sides, 1 <= L <= min(H, W, 32);
-                                   duplicates are ignored                           */
+                                   a repeated side is ignored when it repeats its
+                                   bound (EXPLICIT), EINVAL otherwise            */
     int n_sides;
     double alpha;               /* confidence, 0 < alpha < 1 (unused for EXPLICIT)  */
     smre_cmode cmode;
@@ -142,6 +143,14 @@ typedef struct {
  * device (the Monte Carlo draws run on it). */
 SMRE_API smre_status smre_bounds(const smre_params *p, double *cS_out);
 
+/* Out-of-memory paths of the create calls (smre_dykstra_create,
+ * smre_batch_create, smre_server_create, smre_admm_create) can be exercised
+ * without exhausting the device: with the environment variable
+ * SMRE_TEST_FAIL_ALLOC=N set, the N-th device or pinned host allocation
+ * (counting from 0) made during one create call fails as if the memory had
+ * run out; the call then returns SMRE_ENOMEM after freeing everything it
+ * allocated before.  Unset, it has no effect. */
+
 /* Validate p, compute the bounds, and allocate every device buffer a
  * projection of an H x W image with these sides needs: the increments q_s of
  * all sets (sum over L of L^2 * H * W values, padded rows), two work images and
@@ -156,10 +165,13 @@ SMRE_API smre_status smre_dykstra_create(const smre_params *p, void *cuda_stream
 /* Dykstra's cyclic projection (Sec. 2.3, Algorithm 2): starting from q_s = 0,
  * repeat cycles over every set in the fixed order (sides descending; for each
  * side L the tilings (L, a, b), a outer, b inner, a, b in 0..L-1; windows of a
- * tiling in parallel) with, per set, y = x + q_s, x = p_s(y) (Eq. dykstra:if),
+ * tiling in parallel) with, per set, y = x + q_s, x = p_s(y) (the projection of Sec. 2.3),
  * q_s = y - x, until the stopping test of the handle's parameters holds or
- * max_cycles cycles ran.  x0, x: H x W float images (host or device).
- * Returns OK, ENOTCONVERGED (cap hit, x valid), EINVAL, ETIMEOUT or ECUDA. */
+ * max_cycles cycles ran.  x0, x: H x W float images (host or device).  The
+ * call waits for the projection (its stopping test runs on the device).
+ * Returns OK, ENOTCONVERGED (cap hit, x valid), EINVAL (bad arguments, or x0
+ * holds a NaN or an infinity: the norm |x_prev| of the first cycle is then not
+ * finite and the run stops there; x is not valid), ETIMEOUT or ECUDA. */
 SMRE_API smre_status smre_dykstra_project(smre_dykstra *h, const float *x0, float *x, smre_result *res);
 
 /* Incomplete Dykstra (Sec. 3.2): with B = 2^K, passes i = 0..K cover the image
@@ -210,9 +222,17 @@ SMRE_API long long smre_dykstra_kernel_launches(const smre_dykstra *h);
  * smre_dykstra_create + smre_dykstra_project (with SMRE_F_GROUP_LAUNCHES) +
  * smre_dykstra_destroy, but keeps every intermediate buffer (increments, work
  * images, norms, control block, per-cycle history) in one static device array
- * of 16 MiB inside the library, which every GPU that loads the library holds
- * until the process exits.  It calls no cudaMalloc, cudaFree or other
- * allocating routine.
+ * of 16 MiB inside the library.  It calls no cudaMalloc, cudaFree or other
+ * allocating routine.  The array itself comes into existence when the CUDA
+ * runtime loads the library's device code on a device: with the runtime's
+ * default lazy loading that happens at the first call of this entry point on
+ * that device, which then allocates the 16 MiB (and may synchronise the
+ * device).  So make one call on each device at start-up -- any size that
+ * fits, even a 1 x 1 image -- before the caller's pool reserves the device's
+ * memory and before any stream capture begins; or set CUDA_MODULE_LOADING=EAGER
+ * so that the array is created when the library loads.  From then on the
+ * device holds the array until the process exits and the calls allocate
+ * nothing.
  *   p:    problem and stopping rule as for smre_dykstra_create (cmode PERSET,
  *         CHI2 or EXPLICIT; MAXSTAT is rejected); p->flags is ignored.
  *   cuda_stream: stream the work runs on (NULL: legacy default stream); the
@@ -221,9 +241,8 @@ SMRE_API long long smre_dykstra_kernel_launches(const smre_dykstra *h);
  *   res:  optional host result, as for smre_dykstra_project.
  * Sizes whose buffers exceed the 16 MiB array (roughly sum_L L^2 * H * W * 4
  * bytes plus two images) are rejected with SMRE_EINVAL and a message naming
- * the bytes needed.  The first call on each device looks up the array's
- * device address (once per device, with that device current); make that first
- * call before any stream capture begins.  All calls share the array and it
+ * the bytes needed.  The first call on each device also looks up the array's
+ * device address (once per device, with that device current).  All calls share the array and it
  * keeps the last call's contents; calls whose work overlaps on the GPU (two
  * streams, two threads) race and corrupt each other.
  * Returns OK, ENOTCONVERGED (cap hit, x valid), EINVAL or ECUDA. */
@@ -299,7 +318,9 @@ SMRE_API smre_status smre_batch_poll(smre_batch *b, int *done, int max_done, int
 /* Copy a stopped image's result into x (height x width, host or device; NULL
  * to discard), fill *res (seconds = host time from submit to the poll that
  * saw it stop), and free its slot and arena.  Returns the image's status
- * (OK or ENOTCONVERGED), or EINVAL for a slot that is empty or not stopped. */
+ * (OK or ENOTCONVERGED; EINVAL when the image held a NaN or an infinity, which
+ * its first cycle's norm shows and which stops that image alone), or EINVAL
+ * for a slot that is empty or not stopped. */
 SMRE_API smre_status smre_batch_retrieve(smre_batch *b, int slot, float *x, smre_result *res);
 
 /* Project n images together and wait: submit all (ENOMEM when they do not

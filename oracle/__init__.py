@@ -246,6 +246,29 @@ def icd(x0, K, cS_level, tol=1e-3, max_sweeps=1000) -> ICDResult:
 
 # ------------------------------------------------------------------- checkers
 
+def icd_reach_mask(H, W, K, differ):
+    """Pixels that tiles with a different sweep count can influence (Sec. 3.2).
+
+    ``differ`` holds one boolean (n_ti, n_tj) array per pass i = 0..K (True:
+    the two runs took a different number of sweeps on that tile).  Such a
+    tile's pixels may differ; a tile of a later pass that overlaps a pixel
+    that may differ starts from different values, so all of its pixels may
+    differ as well.  Returns the H x W boolean mask of those pixels; outside
+    it both runs computed the same arithmetic on the same inputs.
+    """
+    B = 1 << K
+    mask = np.zeros((H, W), bool)
+    for i, (off, ni, nj) in enumerate(icd_tile_grid(H, W, K)):
+        d = np.asarray(differ[i]).reshape(ni, nj)
+        for ti in range(ni):
+            for tj in range(nj):
+                sl = (slice(off + B * ti, off + B * (ti + 1)), slice(off + B * tj, off + B * (tj + 1)))
+                if d[ti, tj] or mask[sl].any():
+                    mask[sl] = True
+    return mask
+
+
+
 def max_violation(x, sides, cS) -> float:
     """max over all windows of (sum x^2 - cS) / cS (Eq. geq); <= 0 means feasible."""
     x = np.ascontiguousarray(x, dtype=np.float64)

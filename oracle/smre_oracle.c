@@ -9,7 +9,7 @@
  *
  * Contents (every function cites the passage it follows):
  *   - weights c_s(alpha)               Sec. 2.1 (fourth-root transform of t_s)
- *   - single-set projection p_s        Sec. 2.3, Eq. (dykstra:if)
+ *   - single-set projection p_s        Sec. 2.3 (projection p_s)
  *   - Dykstra's cyclic projection      Sec. 2.3, Algorithm 2 (with the q-update
  *                                      of the incomplete listing in Sec. 3.2)
  *   - incomplete Dykstra (ICD)         Sec. 3.2 (sets Omega^i, P_incomplete)
@@ -190,7 +190,7 @@ double oracle_maxstat_quantile(int H, int W, int n_sides, const int *sides,
 }
 
 /* ------------------------------------------------------------------------ */
-/* Sec. 2.3, Eq. (dykstra:if): projection of one set, in place on s1          */
+/* Sec. 2.3, projection p_s: projection of one set, in place on s1            */
 /* ------------------------------------------------------------------------ */
 
 /* Project the L x L window at (r, c) of the pitch-W array s1 onto

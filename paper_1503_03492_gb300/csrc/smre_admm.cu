@@ -335,6 +335,7 @@ extern "C" {
 smre_status smre_admm_create(const smre_params *proj, const smre_admm_params *ap, void *cuda_stream,
                              smre_admm **out)
 {
+    const AllocScope scope;
     if (!out || !proj || !ap) return afail(nullptr, SMRE_EINVAL, "proj / ap / out is NULL");
     *out = nullptr;
     if (!(ap->sigma > 0.0) || !std::isfinite(ap->sigma))
@@ -370,9 +371,9 @@ smre_status smre_admm_create(const smre_params *proj, const smre_admm_params *ap
     const size_t n = (size_t)a->H * a->W;
     const int gx = (a->W + kTile - 1) / kTile, gy = (a->H + kTile - 1) / kTile;
     a->blocks = gx * gy;
-    cudaError_t e = cudaMalloc(&a->buf, sizeof(float) * n * 11);
-    if (e == cudaSuccess) e = cudaMalloc(&a->d_part, sizeof(double) * 2 * a->blocks);
-    if (e == cudaSuccess) e = cudaMallocHost(&a->h_part, sizeof(double) * 2 * a->blocks);
+    cudaError_t e = dev_malloc(&a->buf, sizeof(float) * n * 11);
+    if (e == cudaSuccess) e = dev_malloc(&a->d_part, sizeof(double) * 2 * a->blocks);
+    if (e == cudaSuccess) e = host_malloc(&a->h_part, sizeof(double) * 2 * a->blocks);
     if (e != cudaSuccess) {
         afail(nullptr, e == cudaErrorMemoryAllocation ? SMRE_ENOMEM : SMRE_ECUDA, "allocation: %s",
               cudaGetErrorString(e));

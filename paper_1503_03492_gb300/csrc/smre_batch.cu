@@ -86,10 +86,15 @@ __global__ void __launch_bounds__(kNormThreads) bdecide_kernel(const BDecideArgs
         ctl->cycles = cyc + 1;
         ctl->step = step;
         ctl->prev_norm = prev;
-        const bool conv = A.tol >= 0.0 && (A.tol_relative ? step <= A.tol * prev : step <= A.tol);
+        // a NaN or Inf in x0 shows in the first cycle's norms (|x_prev| is
+        // |x0| there); any non-finite norm ends the image's run with EINVAL
+        const bool bad_in = !isfinite(step) || !isfinite(prev);
+        const bool conv = !bad_in && A.tol >= 0.0 &&
+                          (A.tol_relative ? step <= A.tol * prev : step <= A.tol);
         const bool cap = cyc + 1 >= A.max_cycles;
-        ctl->status = conv || A.tol < 0.0 ? (int)SMRE_OK : (int)SMRE_ENOTCONVERGED;
-        ctl->stop = (conv || cap) ? 1 : 0;
+        ctl->status = bad_in ? (int)SMRE_EINVAL
+                             : (conv || A.tol < 0.0 ? (int)SMRE_OK : (int)SMRE_ENOTCONVERGED);
+        ctl->stop = (conv || cap || bad_in) ? 1 : 0;
     }
 }
 

@@ -214,11 +214,16 @@ smre_status check_batch_params(const smre_batch_params *p, std::vector<int> &sid
     std::stable_sort(sv.begin(), sv.end(), [](auto &x, auto &y) { return x.first < y.first; });
     sides.clear();
     cS.clear();
-    for (auto &pr : sv)
+    for (auto &pr : sv) {
         if (sides.empty() || sides.back() != pr.first) {
             sides.push_back(pr.first);
             cS.push_back(pr.second);
+        } else if (pr.second != cS.back()) {
+            // a repeated side is ignored only when it repeats the bound too
+            return bfail(nullptr, SMRE_EINVAL, "side %d listed twice with different bounds (%g, %g)",
+                         pr.first, cS.back(), pr.second);
         }
+    }
     return SMRE_OK;
 }
 
@@ -414,6 +419,7 @@ size_t smre_batch_image_bytes(const smre_batch_params *p, int height, int width)
 
 smre_status smre_batch_create(const smre_batch_params *p, void *cuda_stream, smre_batch **out)
 {
+    const AllocScope scope;
     if (!out) return bfail(nullptr, SMRE_EINVAL, "out is NULL");
     *out = nullptr;
     std::vector<int> sides;
@@ -477,18 +483,18 @@ smre_status smre_batch_create(const smre_batch_params *p, void *cuda_stream, smr
     }
     CREATE_CK(batch_prepare(b->qtype, b->smem));
     b->arena_bytes = align256(p->device_bytes);
-    CREATE_CK(cudaMalloc(&b->arena, b->arena_bytes));
+    CREATE_CK(dev_malloc(&b->arena, b->arena_bytes));
     b->heap.reset(b->arena_bytes);
-    CREATE_CK(cudaMalloc(&b->d_imgs, sizeof(BImage) * b->max_images));
-    CREATE_CK(cudaMalloc(&b->d_ctl, sizeof(Control) * b->max_images));
+    CREATE_CK(dev_malloc(&b->d_imgs, sizeof(BImage) * b->max_images));
+    CREATE_CK(dev_malloc(&b->d_ctl, sizeof(Control) * b->max_images));
     CREATE_CK(cudaMemset(b->d_ctl, 0, sizeof(Control) * b->max_images));
-    CREATE_CK(cudaMalloc(&b->d_err, sizeof(int)));
+    CREATE_CK(dev_malloc(&b->d_err, sizeof(int)));
     CREATE_CK(cudaMemset(b->d_err, 0, sizeof(int)));
     b->tab_ints = (size_t)b->max_images + b->steps.size() * (2 * (size_t)b->max_images + 1) +
                   (size_t)b->max_images + 1;
-    CREATE_CK(cudaMalloc(&b->d_tab, sizeof(int) * b->tab_ints));
-    CREATE_CK(cudaMallocHost(&b->h_ctl, sizeof(Control) * b->max_images));
-    CREATE_CK(cudaMallocHost(&b->h_err, sizeof(int)));
+    CREATE_CK(dev_malloc(&b->d_tab, sizeof(int) * b->tab_ints));
+    CREATE_CK(host_malloc(&b->h_ctl, sizeof(Control) * b->max_images));
+    CREATE_CK(host_malloc(&b->h_err, sizeof(int)));
     CREATE_CK(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
     memset(b->h_ctl, 0, sizeof(Control) * b->max_images);
     *b->h_err = 0;
@@ -655,6 +661,9 @@ smre_status smre::batch_retrieve_ld(smre_batch *b, int slot, float *x, int ld, s
         res->seconds = sl.t_done - sl.t_submit;
     }
     const int status = c.status;
+    if (status == SMRE_EINVAL)
+        bfail(b, SMRE_EINVAL, "slot %d: the image holds a NaN or an infinity (the first cycle's "
+              "norm is not finite)", slot);
     b->heap.release(sl.off, sl.bytes);
     sl.used = false;
     sl.done = false;

@@ -1,7 +1,7 @@
 // Batched standard Dykstra path on sm_103a: the images of a batch (any mix of
 // sizes up to 2048 columns) share every launch.
 //
-// Paper: Sec. 2.3 (Algorithm 2, projection Eq. dykstra:if) with the increment
+// Paper: Sec. 2.3 (Algorithm 2 with the projection p_s of Sec. 2.3) with the increment
 // update of the Sec. 3.2 listing, applied set by set in the order sides
 // descending, row offset a, column offset b.
 //
@@ -164,7 +164,7 @@ struct WinData<true> {
 };
 
 // Factors of one window from its sum of squares t: x = y * scale with
-// scale = sqrt(cS / t) if t > cS (Eq. dykstra:if); for 16-bit increments sw,
+// scale = sqrt(cS / t) if t > cS (the projection p_s of Sec. 2.3); for 16-bit increments sw,
 // a power of two with |q_i| / sw <= 2^15 from |q_i| <= (1 - scale) sqrt(t),
 // and f = (1 - scale) / sw.  With `exact`, the FP64 sum t64 against cS64
 // decides and gives the scale (the recheck of windows near the boundary).
@@ -575,7 +575,7 @@ __global__ void __launch_bounds__(kThreads, 1) bstep_kernel(const BStepArgs A)
 
             // the consumers share out the pass's windows (nu rows of nv windows):
             // for each, sum the L column sums in column order, take the ball test
-            // of Eq. (dykstra:if) and, for 16-bit increments, pick the window's
+            // of the projection p_s (Sec. 2.3) and, for 16-bit increments, pick the window's
             // power-of-two scale sw with |q_i| / sw <= 2^15 (FP16 holds up to
             // 65504) from |q_i| <= |q_s|_2 = (1 - scale) sqrt(t); the factors go
             // to the window's first column, windows within the band of the test

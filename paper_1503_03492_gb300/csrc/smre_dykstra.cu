@@ -2,7 +2,7 @@
 // cycle-norm reduction, the device-side stopping decision and the optional
 // constraint-violation check.
 //
-// Paper: Sec. 2.3 (Algorithm 2, projection Eq. dykstra:if), with the
+// Paper: Sec. 2.3 (Algorithm 2 with the projection p_s of Sec. 2.3), with the
 // increment update of the Sec. 3.2 listing applied to every set in turn.
 //
 // One cycle visits the tilings (L, a, b) in the order sides descending,
@@ -19,6 +19,8 @@
 // squares of its column, the L column sums of a window are added from shared
 // memory in a fixed order, so every thread of the window sees the same sum.
 #include <cuda_runtime.h>
+
+#include <mutex>
 
 #include <cstdint>
 
@@ -82,7 +84,7 @@ __global__ void __launch_bounds__(1024, 1) group_kernel(const GroupArgs A)
         }
         __syncthreads();
 
-        // window sums (fixed order) and the ball test of Eq. (dykstra:if)
+        // window sums (fixed order) and the ball test of the projection p_s (Sec. 2.3)
         float scale[CPT];
         int v0[CPT];
         bool near = false;
@@ -159,12 +161,23 @@ cudaError_t launch_group_t(const GroupArgs &A, int threads, cudaStream_t s)
 {
     const size_t smem = (size_t)A.pitch * (2 * sizeof(float) + sizeof(double));
     auto k = group_kernel<LB, CPT>;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(kMaxWidth * (2 * sizeof(float) + sizeof(double))));
-        if (e != cudaSuccess) return e;
-        attr_set = true;
+    // the shared-memory opt-in is a per-device setting of the function: once
+    // per device, under a lock (several threads may launch on several devices)
+    constexpr int kDevs = 64;
+    static std::mutex mu;
+    static bool attr_set[kDevs] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kDevs) return cudaErrorInvalidDevice;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!attr_set[dev]) {
+            e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(kMaxWidth * (2 * sizeof(float) + sizeof(double))));
+            if (e != cudaSuccess) return e;
+            attr_set[dev] = true;
+        }
     }
     k<<<A.n_units, threads, smem, s>>>(A);
     return cudaGetLastError();
@@ -245,10 +258,14 @@ __global__ void __launch_bounds__(256) decide_kernel(const double *__restrict__ 
         ctl->cycles = cyc + 1;
         ctl->step = step;
         ctl->prev_norm = prev;
-        const bool conv = tol >= 0.0 && (tol_relative ? step <= tol * prev : step <= tol);
+        // a NaN or Inf in x0 shows in the first cycle's norms (|x_prev| is
+        // |x0| there); any non-finite norm ends the run with EINVAL
+        const bool bad_in = !isfinite(step) || !isfinite(prev);
+        const bool conv = !bad_in && tol >= 0.0 && (tol_relative ? step <= tol * prev : step <= tol);
         const bool cap = cyc + 1 >= max_cycles;
-        ctl->stop = (conv || cap) ? 1 : 0;
-        ctl->status = conv || tol < 0.0 ? (int)SMRE_OK : (int)SMRE_ENOTCONVERGED;
+        ctl->stop = (conv || cap || bad_in) ? 1 : 0;
+        ctl->status = bad_in ? (int)SMRE_EINVAL
+                             : (conv || tol < 0.0 ? (int)SMRE_OK : (int)SMRE_ENOTCONVERGED);
     }
 }
 

@@ -139,14 +139,19 @@ smre_status check_params(const smre_params *p, std::vector<int> &sides, std::vec
         }
         sv.emplace_back(L, c);
     }
-    std::sort(sv.begin(), sv.end(), [](auto &a, auto &b) { return a.first < b.first; });
+    std::stable_sort(sv.begin(), sv.end(), [](auto &a, auto &b) { return a.first < b.first; });
     sides.clear();
     cexp.clear();
-    for (auto &pr : sv)
+    for (auto &pr : sv) {
         if (sides.empty() || sides.back() != pr.first) {
             sides.push_back(pr.first);
             cexp.push_back(pr.second);
+        } else if (pr.second != cexp.back()) {
+            // a repeated side is ignored only when it repeats the bound too
+            return fail(nullptr, SMRE_EINVAL, "side %d listed twice with different bounds (%g, %g)",
+                        pr.first, cexp.back(), pr.second);
         }
+    }
     if (p->cmode != SMRE_C_EXPLICIT && !(p->alpha > 0.0 && p->alpha < 1.0))
         return fail(nullptr, SMRE_EINVAL, "alpha %g outside (0, 1)", p->alpha);
     if ((int)p->cmode < 0 || (int)p->cmode > 3)
@@ -177,8 +182,8 @@ smre_status maxstat_q(const smre_params *p, const std::vector<int> &sides, doubl
     double *mx = nullptr;
     cudaStream_t s = nullptr;
     std::vector<double> all(draws), part(batch);
-    cudaError_t e = cudaMalloc(&img, per * batch * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&mx, 2 * batch * sizeof(double));
+    cudaError_t e = dev_malloc(&img, per * batch * sizeof(float));
+    if (e == cudaSuccess) e = dev_malloc(&mx, 2 * batch * sizeof(double));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
     for (int d0 = 0; e == cudaSuccess && d0 < draws; d0 += batch) {
         const int n = std::min(batch, draws - d0);
@@ -296,8 +301,15 @@ smre_status autotune(smre_dykstra *h)
             v = (float)((double)(z >> 11) * (6.0 / 9007199254740992.0) - 3.0);
         }
         float *xt = nullptr;
-        CK(h, cudaMalloc(&xt, sizeof(float) * img.size()));
-        CK(h, cudaMemcpy(xt, img.data(), sizeof(float) * img.size(), cudaMemcpyHostToDevice));
+        CK(h, dev_malloc(&xt, sizeof(float) * img.size()));
+        {
+            const cudaError_t e = cudaMemcpy(xt, img.data(), sizeof(float) * img.size(),
+                                             cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) {
+                cudaFree(xt);
+                return fail(h, SMRE_ECUDA, "autotune image: %s", cudaGetErrorString(e));
+            }
+        }
         const int mc = h->max_cycles;
         const double tol = h->tol;
         const int rel = h->tol_relative;
@@ -336,7 +348,7 @@ smre_status autotune(smre_dykstra *h)
         // the batch holds the increments: drop the handle's own store
         cudaFree(h->q);
         h->q = nullptr;
-        CK(h, cudaMalloc(&h->q, sizeof(float)));
+        CK(h, dev_malloc(&h->q, sizeof(float)));
         h->dev_bytes -= sizeof(float) * (h->q_floats - 1);
         h->q_floats = 0;
     }
@@ -411,7 +423,7 @@ smre_status ensure_hist(smre_dykstra *h, int cap)
         h->dev_bytes -= sizeof(double) * 2 * h->hist_cap;
         h->hist = nullptr;
     }
-    CK(h, cudaMalloc(&h->hist, sizeof(double) * 2 * cap));
+    CK(h, dev_malloc(&h->hist, sizeof(double) * 2 * cap));
     h->hist_cap = cap;
     h->dev_bytes += sizeof(double) * 2 * cap;
     return SMRE_OK;
@@ -701,22 +713,22 @@ smre_status plan_persistent(smre_dykstra *h, int flags)
     auto up = [&](auto **dptr, const auto &vec) -> cudaError_t {
         using E = typename std::remove_reference<decltype(vec[0])>::type;
         const size_t bytes = sizeof(E) * std::max<size_t>(vec.size(), 1);
-        cudaError_t e = cudaMalloc((void **)dptr, bytes);
+        cudaError_t e = dev_malloc((void **)dptr, bytes);
         if (e != cudaSuccess) return e;
         h->dev_bytes += bytes;
         return cudaMemcpy(*dptr, vec.data(), sizeof(E) * vec.size(), cudaMemcpyHostToDevice);
     };
     CK(h, up(&h->d_sched, sched));
     CK(h, up(&h->d_cta_off, cta_off));
-    CK(h, cudaMalloc(&h->d_flags, sizeof(unsigned) * std::max(nflag_all, 1)));
-    CK(h, cudaMalloc(&h->d_barrier, 128));   // [0]: per-cycle grid barrier, [16]: launch prologue
-    CK(h, cudaMalloc(&h->d_selftest, 64));
+    CK(h, dev_malloc(&h->d_flags, sizeof(unsigned) * std::max(nflag_all, 1)));
+    CK(h, dev_malloc(&h->d_barrier, 128));   // [0]: per-cycle grid barrier, [16]: launch prologue
+    CK(h, dev_malloc(&h->d_selftest, 64));
     CK(h, cudaMemset(h->d_selftest, 0, 64));
-    CK(h, cudaMalloc(&h->d_abort, 64));
-    CK(h, cudaMalloc(&h->d_ppartials, sizeof(double) * 4 * G));
+    CK(h, dev_malloc(&h->d_abort, 64));
+    CK(h, dev_malloc(&h->d_ppartials, sizeof(double) * 4 * G));
     // zero source of the first cycle's copies (one unit-pass of rows at most)
     const size_t zero_floats = reg ? (size_t)stage_floats : (size_t)stage_floats / sp * pitch;
-    CK(h, cudaMalloc(&h->d_zeros, sizeof(float) * zero_floats));
+    CK(h, dev_malloc(&h->d_zeros, sizeof(float) * zero_floats));
     CK(h, cudaMemset(h->d_zeros, 0, sizeof(float) * zero_floats));
     h->dev_bytes += sizeof(unsigned) * nflag_all + 192 + sizeof(double) * 4 * G +
                     sizeof(float) * zero_floats;
@@ -727,9 +739,9 @@ smre_status plan_persistent(smre_dykstra *h, int flags)
         // words per event, zero (no valid tag) until first written
         h->xch_words = (size_t)std::max(nflags, 1) * pitch;
         const size_t xbytes = sizeof(unsigned long long) * h->xch_words;
-        CK(h, cudaMalloc(&h->d_xch, xbytes));
+        CK(h, dev_malloc(&h->d_xch, xbytes));
         CK(h, cudaMemset(h->d_xch, 0, xbytes));
-        CK(h, cudaMalloc(&h->d_smid, sizeof(unsigned) * G));
+        CK(h, dev_malloc(&h->d_smid, sizeof(unsigned) * G));
         h->dev_bytes += xbytes + sizeof(unsigned) * G;
     }
     h->p_sp = sp;
@@ -869,12 +881,18 @@ smre_status project_core(smre_dykstra *h, const float *x0, float *x, smre_result
     }
     st = stage_out(h, x);
     if (st != SMRE_OK) return st;
+    // the device's status (every schedule has its control block on the host by now)
+    const int dev_status = h->ctl_host->status;
+    if (dev_status == SMRE_EINVAL)
+        fail(h, SMRE_EINVAL, "x0 holds a NaN or an infinity (the first cycle's norm is not finite)");
+    else if (dev_status == SMRE_ETIMEOUT)
+        fail(h, SMRE_ETIMEOUT, "a device-side wait ran out of time; the result is not valid");
     if (res) {
         CK(h, cudaStreamSynchronize(h->stream));
         float ms = 0.f;
         CK(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
         res->cycles = h->ctl_host->cycles;
-        res->status = h->ctl_host->status;
+        res->status = dev_status;
         res->step = h->ctl_host->step;
         res->rel_step = h->ctl_host->prev_norm > 0 ? h->ctl_host->step / h->ctl_host->prev_norm : 0.0;
         res->max_violation = viol;
@@ -883,18 +901,59 @@ smre_status project_core(smre_dykstra *h, const float *x0, float *x, smre_result
         res->seconds = ms * 1e-3;
         return (smre_status)res->status;
     }
-    return SMRE_OK;
+    return (smre_status)dev_status;
 }
 
 }  // namespace
 
 namespace smre {
 void set_thread_error(const char *msg) { g_err = msg; }
+
+namespace {
+thread_local int g_alloc_depth = 0;     // create calls in progress on this thread
+thread_local long g_alloc_count = 0;    // allocations made since the outermost began
+thread_local long g_alloc_fail = -1;    // index of the allocation that fails (-1: none)
+
+bool alloc_should_fail()
+{
+    if (g_alloc_depth == 0 || g_alloc_fail < 0) return false;
+    return g_alloc_count++ == g_alloc_fail;
+}
+}  // namespace
+
+AllocScope::AllocScope()
+{
+    if (g_alloc_depth++ == 0) {
+        g_alloc_count = 0;
+        const char *e = getenv("SMRE_TEST_FAIL_ALLOC");
+        g_alloc_fail = (e && *e) ? atol(e) : -1;
+    }
+}
+
+AllocScope::~AllocScope() { --g_alloc_depth; }
+
+cudaError_t dev_malloc(void **p, size_t bytes)
+{
+    if (alloc_should_fail()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
+cudaError_t host_malloc(void **p, size_t bytes)
+{
+    if (alloc_should_fail()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMallocHost(p, bytes);
+}
 }  // namespace smre
 
 extern "C" {
 
-const char *smre_version(void) { return "smre-gb300 0.7 (sm_103a)"; }
+const char *smre_version(void) { return "smre-gb300 0.8 (sm_103a)"; }
 
 const char *smre_last_error(const smre_dykstra *h)
 {
@@ -921,6 +980,7 @@ smre_status smre_bounds(const smre_params *p, double *cS_out)
 
 smre_status smre_dykstra_create(const smre_params *p, void *cuda_stream, smre_dykstra **out)
 {
+    const AllocScope scope;
     if (!out) return fail(nullptr, SMRE_EINVAL, "out is NULL");
     *out = nullptr;
     std::vector<int> sides;
@@ -975,17 +1035,17 @@ smre_status smre_dykstra_create(const smre_params *p, void *cuda_stream, smre_dy
     } while (0)
 
     const size_t img = sizeof(float) * (size_t)h->H * h->pitch;
-    CKC(cudaMalloc(&h->q, sizeof(float) * std::max<size_t>(h->q_floats, 1)));
-    CKC(cudaMalloc(&h->xw, img));
-    CKC(cudaMalloc(&h->xprev, img));
+    CKC(dev_malloc(&h->q, sizeof(float) * std::max<size_t>(h->q_floats, 1)));
+    CKC(dev_malloc(&h->xw, img));
+    CKC(dev_malloc(&h->xprev, img));
     CKC(cudaMemset(h->xw, 0, img));
     CKC(cudaMemset(h->xprev, 0, img));
     h->n_partials = norm_blocks();
-    CKC(cudaMalloc(&h->partials, sizeof(double) * 2 * h->n_partials));
-    CKC(cudaMalloc(&h->ctl, sizeof(Control)));
-    CKC(cudaMalloc(&h->viol, sizeof(double)));
-    CKC(cudaMallocHost(&h->ctl_host, sizeof(Control)));
-    CKC(cudaMallocHost(&h->viol_host, sizeof(double)));
+    CKC(dev_malloc(&h->partials, sizeof(double) * 2 * h->n_partials));
+    CKC(dev_malloc(&h->ctl, sizeof(Control)));
+    CKC(dev_malloc(&h->viol, sizeof(double)));
+    CKC(host_malloc(&h->ctl_host, sizeof(Control)));
+    CKC(host_malloc(&h->viol_host, sizeof(double)));
     CKC(cudaEventCreate(&h->ev0));
     CKC(cudaEventCreate(&h->ev1));
     h->dev_bytes = sizeof(float) * std::max<size_t>(h->q_floats, 1) + 2 * img +
@@ -993,8 +1053,10 @@ smre_status smre_dykstra_create(const smre_params *p, void *cuda_stream, smre_dy
     if (ensure_hist(h, h->max_cycles) != SMRE_OK) return bail(SMRE_ENOMEM);
     if (tune) {
         // every schedule that can run the shape, then time them
-        if (p->q_dtype == SMRE_Q_FP32 && plan_persistent(h, p->flags) != SMRE_OK)
-            return bail(SMRE_ECUDA);
+        if (p->q_dtype == SMRE_Q_FP32) {
+            st = plan_persistent(h, p->flags);
+            if (st != SMRE_OK) return bail(st);
+        }
         if (batch_fits) {
             st = make_handle_batch(h);
             if (st != SMRE_OK) return bail(st);
@@ -1004,8 +1066,9 @@ smre_status smre_dykstra_create(const smre_params *p, void *cuda_stream, smre_dy
     } else if (batched) {
         st = make_handle_batch(h);
         if (st != SMRE_OK) return bail(st);
-    } else if (plan_persistent(h, p->flags) != SMRE_OK) {
-        return bail(SMRE_ECUDA);
+    } else {
+        st = plan_persistent(h, p->flags);
+        if (st != SMRE_OK) return bail(st);
     }
 #undef CKC
     *out = h;
@@ -1074,7 +1137,7 @@ smre_status smre_dykstra_project_incomplete(smre_dykstra *h, const float *x0, fl
             h->dev_bytes -= sizeof(int) * h->icd_sweeps_cap;
             h->icd_sweeps = nullptr;
         }
-        CK(h, cudaMalloc(&h->icd_sweeps, sizeof(int) * std::max(total, 1)));
+        CK(h, dev_malloc(&h->icd_sweeps, sizeof(int) * std::max(total, 1)));
         h->icd_sweeps_cap = std::max(total, 1);
         h->dev_bytes += sizeof(int) * h->icd_sweeps_cap;
     }

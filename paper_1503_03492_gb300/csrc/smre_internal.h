@@ -266,6 +266,21 @@ cudaError_t launch_icd_pass(const IcdArgs &a, cudaStream_t s);
 // Message returned by smre_last_error(NULL) on this thread (smre_host.cu).
 void set_thread_error(const char *msg);
 
+// Device and pinned host allocations (smre_host.cu).  With the environment
+// variable SMRE_TEST_FAIL_ALLOC=N set, the N-th allocation (counting from 0)
+// made inside the outermost create call of this thread fails with
+// cudaErrorMemoryAllocation and allocates nothing: a test aid that drives
+// every out-of-memory path of the create calls.  AllocScope marks a create
+// call (nested creates share the outer count).
+cudaError_t dev_malloc(void **p, size_t bytes);
+cudaError_t host_malloc(void **p, size_t bytes);
+template <class T> inline cudaError_t dev_malloc(T **p, size_t bytes) { return dev_malloc((void **)p, bytes); }
+template <class T> inline cudaError_t host_malloc(T **p, size_t bytes) { return host_malloc((void **)p, bytes); }
+struct AllocScope {
+    AllocScope();
+    ~AllocScope();
+};
+
 // Host FP64 helpers of Sec. 2.1 (smre_weights.cu).
 double inv_normal_cdf(double p);
 double chi2_quantile(double alpha, int k);

@@ -7,9 +7,13 @@
 // (it may synchronise the device) in the middle of their frame budget.
 // smre_dykstra_project_static serves them: every buffer the projection needs
 // besides the caller's input and output lives in one file-scope device array
-// of kStaticScratchBytes, which each GPU that loads the library holds until the
-// process exits.  It runs the same group kernels as the handle-based
-// SMRE_F_GROUP_LAUNCHES schedule, so its results are the same.
+// of kStaticScratchBytes.  The runtime creates that array when it loads this
+// library's device code on a device -- with its default lazy loading, at the
+// first cudaGetSymbolAddress below, i.e. the first call on that device, which
+// therefore allocates (and may synchronise): callers make that first call at
+// start-up, or set CUDA_MODULE_LOADING=EAGER.  The device then holds the array
+// until the process exits.  The entry point runs the same group kernels as the
+// handle-based SMRE_F_GROUP_LAUNCHES schedule, so its results are the same.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -115,6 +119,10 @@ extern "C" smre_status smre_dykstra_project_static(const smre_params *p, void *c
         if (std::find(sides.begin(), sides.end(), L) == sides.end()) {
             sides.push_back(L);
             cS_of[L] = c;
+        } else if (c != cS_of[L]) {
+            // a repeated side is ignored only when it repeats the bound too
+            return reject(SMRE_EINVAL, "side %d listed twice with different bounds (%g, %g)", L,
+                          cS_of[L], c);
         }
     }
     std::sort(sides.rbegin(), sides.rend());

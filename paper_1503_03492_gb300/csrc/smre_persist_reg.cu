@@ -993,9 +993,13 @@ __global__ void __launch_bounds__((NW + 2) * 32, 1) persist_reg_kernel(const __g
                     N += s_red[1][w];
                 }
                 const double step = sqrt(D), prev = sqrt(N);
-                const bool conv = A.tol >= 0.0 && (A.tol_relative ? step <= A.tol * prev : step <= A.tol);
+                // a NaN or Inf in x0 shows in the first cycle's norms (|x_prev| is
+                // |x0| there); any non-finite norm ends the run with EINVAL
+                const bool bad_in = !isfinite(step) || !isfinite(prev);
+                const bool conv = !bad_in && A.tol >= 0.0 &&
+                                  (A.tol_relative ? step <= A.tol * prev : step <= A.tol);
                 const bool cap = cyc + 1 >= A.max_cycles;
-                dec = (conv || cap) ? kStop : kGo;
+                dec = (conv || cap || bad_in) ? kStop : kGo;
                 if (cta == 0 && tid == 0) {
                     if (cyc < A.hist_cap) {
                         A.hist[2 * cyc] = step;
@@ -1006,7 +1010,9 @@ __global__ void __launch_bounds__((NW + 2) * 32, 1) persist_reg_kernel(const __g
                     A.ctl->prev_norm = prev;
                     if (dec == kStop) {
                         A.ctl->stop = 1;
-                        if (!conv && A.tol >= 0.0)
+                        if (bad_in)
+                            atomicCAS(&A.ctl->status, (int)SMRE_OK, (int)SMRE_EINVAL);
+                        else if (!conv && A.tol >= 0.0)
                             atomicCAS(&A.ctl->status, (int)SMRE_OK, (int)SMRE_ENOTCONVERGED);
                     }
                 }

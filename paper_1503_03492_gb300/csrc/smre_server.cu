@@ -170,6 +170,7 @@ extern "C" {
 
 smre_status smre_server_create(const smre_server_params *p, void *cuda_stream, smre_server **out)
 {
+    const AllocScope scope;
     if (!out || !p) {
         set_thread_error("params / out is NULL");
         return SMRE_EINVAL;

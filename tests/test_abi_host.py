@@ -57,6 +57,17 @@ def test_host_bounds_explicit_and_order(smre):
     assert smre.smre_bounds(p) == [5.0, 1.5, 3.0]
 
 
+def test_repeated_side_needs_the_same_bound(smre):
+    """A side listed twice is ignored when it repeats its bound; with two
+    different explicit bounds the call fails (no schedule could honour both)."""
+    p = smre.make_params(32, 32, [2, 1, 2], cmode=smre.SMRE_C_EXPLICIT, c_explicit=[3.0, 1.5, 3.0])
+    assert smre.smre_bounds(p) == [3.0, 1.5, 3.0]
+    p = smre.make_params(32, 32, [2, 1, 2], cmode=smre.SMRE_C_EXPLICIT, c_explicit=[3.0, 1.5, 4.0])
+    with pytest.raises(smre.SmreError) as ei:
+        smre.smre_bounds(p)
+    assert ei.value.status == smre.SMRE_EINVAL and "twice" in str(ei.value)
+
+
 @pytest.mark.parametrize("kw,msg", [
     (dict(H=0, W=8, sides=[1]), "out of range"),
     (dict(H=8, W=5000, sides=[1]), "width"),

@@ -50,7 +50,10 @@ def run_std(smre, torch, x0, sides, cS, max_cycles, tol=-1.0, rel=False, flags=0
         return out.cpu().numpy(), res, hist
 
 
-PATHS = {"persistent": 0, "group": 2}   # 2 = SMRE_F_GROUP_LAUNCHES
+# 0: the register-band persistent kernel where the shape fits it, 16 =
+# SMRE_F_BAND_IN_SMEM: the shared-memory band persistent kernel, 2 =
+# SMRE_F_GROUP_LAUNCHES: one group-kernel launch per (side, offset) group
+PATHS = {"persistent": 0, "persistent_smem_band": 16, "group": 2}
 
 
 def f32(x):
@@ -92,10 +95,12 @@ def test_persistent_and_group_paths_agree_bitwise(smre, torch_cuda, oracle_mod, 
     a, ra, ha, la = run_std(smre, torch_cuda, x0, sides, cS, 5, want_launches=True)
     b, rb, hb, lb = run_std(smre, torch_cuda, x0, sides, cS, 5, flags=PATHS["group"],
                             want_launches=True)
-    assert la == 1, la                      # one cooperative launch for all cycles
+    c, rc, hc, lc = run_std(smre, torch_cuda, x0, sides, cS, 5, flags=PATHS["persistent_smem_band"],
+                            want_launches=True)
+    assert la == 1 and lc == 1, (la, lc)    # one cooperative launch for all cycles
     assert lb > 5 * len(set(sides))
-    assert np.array_equal(a, b)
-    assert np.allclose(ha, hb, rtol=1e-12)
+    assert np.array_equal(a, b) and np.array_equal(a, c)
+    assert np.allclose(ha, hb, rtol=1e-12) and np.allclose(ha, hc, rtol=1e-12)
 
 
 def test_persistent_timeout_is_reported_and_handle_survives(smre, torch_cuda, oracle_mod):
@@ -246,21 +251,58 @@ def test_icd_fixed_sweeps_matches_oracle(smre, torch_cuda, oracle_mod, H, W, K):
         assert err(got, ref.x) <= TOL, (sweeps, err(got, ref.x))
 
 
+def icd_compare(oracle_mod, got, sw, ref, K):
+    """Values of the GPU's incomplete projection against the oracle's, with
+    the stopping decisions compared as well: a tile's sweep count may differ
+    only where its L1 change lies within FP32 rounding of tol * B^2, and then
+    the pixels it and the later tiles overlapping it can reach are left out
+    of the value comparison (oracle.icd_reach_mask); everywhere else the error
+    must meet the FP32 bar.  Returns (agreement, error outside, reach share)."""
+    H, W = got.shape
+    ref_sw = np.concatenate([s.ravel() for s in ref.sweeps])
+    differ, o = [], 0
+    for (_, ni, nj) in ref.grid:
+        differ.append((sw[o:o + ni * nj] != ref_sw[o:o + ni * nj]).reshape(ni, nj))
+        o += ni * nj
+    mask = oracle_mod.icd_reach_mask(H, W, K, differ)
+    scale = max(np.abs(ref.x).max(), 1e-300)
+    e = float(np.abs(np.asarray(got, np.float64) - ref.x)[~mask].max() / scale) if (~mask).any() else 0.0
+    return float((sw == ref_sw).mean()), e, float(mask.mean())
+
+
 def test_icd_paper_tolerance_512(smre, torch_cuda, oracle_mod, emitter512):
-    """512 x 512 emitters, K = 3 (sides 1, 2, 4, 8), the paper's tol 1e-3.
-    Tiles whose sweep count agrees must agree in value; disagreements can only
-    come from an L1 change within FP32 rounding of tol * B^2."""
+    """512 x 512 emitters, K = 3 (sides 1, 2, 4, 8), the paper's tol 1e-3 --
+    the benchmark's incomplete configuration.  Values are always compared:
+    everywhere outside the reach of tiles whose sweep count differs."""
     x0, _, _ = emitter512
     sides = [1, 2, 4, 8]
     cS = oracle_mod.bounds(sides, 0.9)
     got, res, sw = run_icd(smre, torch_cuda, x0, sides, cS, 3, 1e-3)
     ref = oracle_mod.icd(x0.astype(np.float64), 3, cS, tol=1e-3)
-    ref_sw = np.concatenate([s.ravel() for s in ref.sweeps])
-    agree = (sw == ref_sw).mean()
+    agree, e, reach = icd_compare(oracle_mod, got, sw, ref, 3)
     assert agree >= 0.99, agree
-    if agree == 1.0:
-        assert err(got, ref.x) <= TOL, err(got, ref.x)
+    assert reach <= 0.05, reach
+    assert e <= TOL, e
     assert res.windows > 0 and res.max_tile_sweeps == sw.max()
+
+
+@pytest.mark.parametrize("K", [1, 2, 3, 4, 5])
+def test_icd_stop_threshold_on_gpu(smre, torch_cuda, oracle_mod, K):
+    """The stopping threshold tol * B^2 through the C ABI: a B x B image of one
+    constant v takes two sweeps when its first sweep's L1 change is 1 % above
+    tol * B^2 and one when it is 1 % below (the closed form of the oracle
+    pin)."""
+    B = 1 << K
+    sides = [1 << k for k in range(K + 1)]
+    cS = oracle_mod.bounds(sides, 0.9)
+    tol = 1e-3
+    for f, want in ((1.01, 2), (0.99, 1)):
+        v = np.sqrt(cS[K]) / B + f * tol
+        x0 = np.full((B, B), v, np.float32)
+        got, res, sw = run_icd(smre, torch_cuda, x0, sides, cS, K, tol, 100)
+        assert sw.tolist() == [want], (f, sw)
+        ref = x0.astype(np.float64) * np.sqrt(cS[K] / (B * B * float(x0[0, 0]) ** 2))
+        assert err(got, ref) <= TOL
 
 
 def test_icd_tight_tolerance(smre, torch_cuda, oracle_mod):
@@ -271,6 +313,33 @@ def test_icd_tight_tolerance(smre, torch_cuda, oracle_mod):
     got, _, _ = run_icd(smre, torch_cuda, x0, sides, cS, 3, 1e-9, 3000)
     ref = oracle_mod.icd(x0.astype(np.float64), 3, cS, tol=1e-12, max_sweeps=3000)
     assert err(got, ref.x) <= TOL, err(got, ref.x)
+
+
+# --------------------------------------------------- non-finite input
+
+@pytest.mark.parametrize("flags,q_dtype,H,W", [(0, 0, 64, 80), (16, 0, 64, 80), (2, 0, 64, 80),
+                                               (0, 1, 64, 80), (0, 0, 40, 1500)])
+@pytest.mark.parametrize("bad", [np.nan, np.inf, -np.inf])
+def test_non_finite_input_is_rejected(smre, torch_cuda, oracle_mod, flags, q_dtype, H, W, bad):
+    """A NaN or an infinity in x0 shows in the first cycle's norm |x_prev| on
+    the device: every schedule (register band, shared-memory band, group
+    launches, one-image batch with 16-bit or wide FP32 images) stops there and
+    returns SMRE_EINVAL; the handle then projects a finite image normally."""
+    sides = [1, 2, 3]
+    cS = oracle_mod.bounds(sides, 0.9)
+    x0 = f32(np.random.default_rng(5).standard_normal((H, W)) * 3)
+    xb = x0.copy()
+    xb[H // 2, W // 3] = bad
+    with smre.Projector(H, W, sides, cmode=smre.SMRE_C_EXPLICIT, c_explicit=list(cS),
+                        max_cycles=50, tol=1e-8, tol_relative=True, flags=flags,
+                        q_dtype=q_dtype) as P:
+        out = np.empty_like(x0)
+        with pytest.raises(smre.SmreError) as ei:
+            P.project(xb, out)
+        assert ei.value.status == smre.SMRE_EINVAL
+        assert "NaN" in str(ei.value) or "infinity" in str(ei.value)
+        res = P.project(x0, out)
+        assert res.cycles >= 1 and np.isfinite(out).all()
 
 
 # ------------------------------------------------------------ bounds

@@ -5,7 +5,7 @@ a convex-analysis property or a brute-force solution, chosen so that a
 plausible mistake (a dropped term, a wrong sign or index, a transposed operand,
 a wrong set order or offset) fails at least one of them.
 
-Paper passages: weights Sec. 2.1; projection Eq. (dykstra:if) and Algorithm 2
+Paper passages: weights Sec. 2.1; projection p_s of Sec. 2.3 and Algorithm 2
 (Sec. 2.3); incomplete Dykstra Sec. 3.2.
 """
 import numpy as np
@@ -296,6 +296,47 @@ def test_icd_K0_is_elementwise_clamp(oracle_mod):
     # one set per tile: a feasible pixel ends after one sweep; otherwise the
     # second sweep changes nothing and ends the tile
     assert np.array_equal(r.sweeps[0], np.where(np.abs(x0) > np.sqrt(2.0), 2, 1))
+
+
+@pytest.mark.parametrize("K", [1, 2, 3, 4, 5])
+def test_icd_stop_threshold_is_tol_times_B_squared(oracle_mod, K):
+    """The tile's sweep loop ends when one sweep changes e by at most tol * B^2
+    in L1 (Sec. 3.2 listing: tol * 1024 for B = 32).  A B x B image of one
+    constant v has a single tile, in the last pass, holding a single set (the
+    whole tile): the first sweep projects it onto the ball and changes it by
+    B^2 v - B sqrt(c) in L1, the second sweep changes nothing.  So the tile
+    takes two sweeps when v is a little above tol + sqrt(c) / B and one when
+    it is a little below -- a threshold of tol * B or tol * B^4 would give the
+    same count on both sides."""
+    B = 1 << K
+    c = oracle_mod.bounds([1 << k for k in range(K + 1)], 0.9)
+    tol = 1e-3
+    for f, want in ((1.01, 2), (0.99, 1)):
+        v = np.sqrt(c[K]) / B + f * tol
+        x0 = np.full((B, B), v)
+        r = oracle_mod.icd(x0, K, c, tol=tol, max_sweeps=100)
+        assert all(s.size == 0 for s in r.sweeps[:K])      # shifted tiles do not fit
+        assert r.sweeps[K].shape == (1, 1) and int(r.sweeps[K][0, 0]) == want, (f, r.sweeps[K])
+        # the change of the first sweep is f * tol * B^2 by construction
+        assert abs(np.abs(x0 - r.x).sum() - f * tol * B * B) < 1e-9 * B * B
+        # and the result is the projection of the tile onto its ball
+        assert np.abs(r.x - x0 * np.sqrt(c[K] / (B * B * v * v))).max() < 1e-14
+
+
+def test_icd_reach_mask(oracle_mod):
+    """A tile with a different sweep count taints its pixels and, through
+    them, every later-pass tile that overlaps them (and nothing else)."""
+    H, W, K = 20, 20, 2        # B = 4: pass 0 offset 1, pass 1 offset 2, pass 2 offset 0
+    grid = oracle_mod.icd_tile_grid(H, W, K)
+    differ = [np.zeros((ni, nj), bool) for (_, ni, nj) in grid]
+    differ[0][1, 1] = True     # pass 0 tile at rows/cols 5..8
+    m = oracle_mod.icd_reach_mask(H, W, K, differ)
+    ref = np.zeros((H, W), bool)
+    ref[5:9, 5:9] = True                 # the tile itself
+    ref[2:10, 2:10] = True               # pass 1 tiles (offset 2) overlapping rows/cols 5..8: 2..5, 6..9
+    ref[0:12, 0:12] = True               # pass 2 tiles (offset 0) overlapping 2..9: 0..3, 4..7, 8..11
+    assert np.array_equal(m, ref)
+    assert not oracle_mod.icd_reach_mask(H, W, K, [np.zeros_like(d) for d in differ]).any()
 
 
 def test_icd_tile_grid_offsets(oracle_mod):

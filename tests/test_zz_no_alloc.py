@@ -53,6 +53,34 @@ def test_static_entry_point_matches_allocating_path_twice(torch_cuda):
         assert e <= TOL, (call, e)
 
 
+def test_static_entry_point_allocates_nothing_after_warm_up(torch_cuda):
+    """After one warm-up call (which makes the runtime load the library's
+    device code, the static array with it), further calls leave the device's
+    free memory unchanged; host images work too."""
+    import paper_1503_03492_gb300 as smre
+    from synthetic import emitter_residual
+
+    H, W, sides = 64, 72, [1, 2, 4]
+    cS = smre.smre_bounds(smre.make_params(H, W, sides, alpha=0.9))
+    kw = dict(cmode=smre.SMRE_C_EXPLICIT, c_explicit=cS, max_cycles=10, tol=-1.0)
+    p = smre.make_params(H, W, sides, **kw)
+    x0 = np.ascontiguousarray(emitter_residual(H, W, n_emitters=8, seed=21), np.float32)
+    out = np.empty_like(x0)
+    smre.smre_dykstra_project_static(p, x0, out)          # warm-up (host images)
+    torch_cuda.cuda.synchronize()
+    free0 = torch_cuda.cuda.mem_get_info()[0]
+    out2 = np.full_like(x0, np.nan)
+    r = smre.smre_dykstra_project_static(p, x0, out2)
+    torch_cuda.cuda.synchronize()
+    assert torch_cuda.cuda.mem_get_info()[0] == free0
+    assert r.cycles == 10
+    with smre.Projector(H, W, sides, **kw) as P:
+        ref = np.empty_like(x0)
+        P.project(x0, ref)
+    assert _err(out2, ref) <= TOL
+    assert np.array_equal(out, out2)
+
+
 def test_static_entry_point_rejects_sizes_beyond_its_buffer(torch_cuda):
     import paper_1503_03492_gb300 as smre
 
