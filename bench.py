@@ -253,18 +253,23 @@ def windows_per_cycle(shapes, sides):
     return sum((h - L + 1) * (w - L + 1) for (h, w) in shapes for L in sides)
 
 
-def timed_batch_cycles(smre, torch, xs, sides, cS, qdt, cycles, stream):
+def timed_batch_cycles(smre, torch, xs, sides, cS, qdt, cycles, stream, tune=False):
     """Per-cycle device time of a batch over xs (device tensors): the first
-    cycle (no increments to read) runs untimed, then `cycles` timed."""
+    cycle (no increments to read) runs untimed -- with tune, the autotuner's
+    cycles too (one untimed, one per candidate spread) -- then `cycles`
+    timed.  Returns (seconds per cycle, launches, (spread, tuned))."""
+    warm = 4 if tune else 1
     need = sum(smre.smre_batch_image_bytes(smre.make_batch_params(sides, q_dtype=qdt,
-                                                                  max_cycles=cycles + 1), *x.shape)
+                                                                  max_cycles=cycles + warm), *x.shape)
                for x in xs)
     with smre.Batch(sides, stream=stream, cmode=smre.SMRE_C_EXPLICIT, c_explicit=cS, q_dtype=qdt,
-                    max_cycles=cycles + 1, tol=-1.0, max_images=len(xs),
-                    device_bytes=need + (64 << 20)) as B:
+                    max_cycles=cycles + warm, tol=-1.0, max_images=len(xs),
+                    device_bytes=need + (64 << 20),
+                    flags=smre.SMRE_BF_AUTOTUNE if tune else 0) as B:
         for x in xs:
             assert B.submit(x) >= 0
-        B.run(1)
+        B.run(warm)
+        spread = B.item_spread()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         B.run(cycles)
@@ -275,7 +280,7 @@ def timed_batch_cycles(smre, torch, xs, sides, cS, qdt, cycles, stream):
         for s in done:
             outs[s] = B.retrieve(s)
         launches = B.kernel_launches()
-    return e0.elapsed_time(e1) / 1e3 / cycles, launches
+    return e0.elapsed_time(e1) / 1e3 / cycles, launches, spread
 
 
 def bench_batched(smre, torch, stream, peak):
@@ -292,10 +297,15 @@ def bench_batched(smre, torch, stream, peak):
            "windows_per_cycle": wpc}
     cycles = 4
     for name, qdt in (("bf16", smre.SMRE_Q_BF16), ("fp32", smre.SMRE_Q_FP32)):
-        sec, _ = timed_batch_cycles(smre, torch, xs, SIDES, cS, qdt, cycles, stream)
+        sec, _, (spread, tuned) = timed_batch_cycles(smre, torch, xs, SIDES, cS, qdt, cycles, stream,
+                                                     tune=True)
         gbs = q_bytes_per_cycle(shapes, SIDES, qdt) / sec / 1e9
         out[name] = {"ms_per_cycle": 1e3 * sec, "window_projections_per_s": wpc / sec,
-                     "achieved_gbs": gbs, "frac_of_measured_hbm": gbs / peak}
+                     "achieved_gbs": gbs, "frac_of_measured_hbm": gbs / peak,
+                     "item_spread": spread, "spread_autotuned": {1: "measured", 2: "cached"}.get(tuned, "no")}
+        # the untuned launches (spread 1) beside the tuned ones
+        sec1, _, _ = timed_batch_cycles(smre, torch, xs, SIDES, cS, qdt, cycles, stream)
+        out[name]["ms_per_cycle_spread1"] = 1e3 * sec1
     # one launch per image (FP32 single-image API), on the first 24 images
     tot_w, tot_s = 0, 0.0
     for x in xs[:24]:
@@ -309,6 +319,9 @@ def bench_batched(smre, torch, stream, peak):
             tot_s += r.seconds
     out["one_launch_per_image_fp32"] = {"window_projections_per_s": tot_w / tot_s,
                                         "sample": "first 24 images, 3 cycles each"}
+    # at equal precision (FP32 increments on both sides), and BF16 beside it
+    out["speedup_fp32_vs_one_launch_per_image"] = (out["fp32"]["window_projections_per_s"] /
+                                                   (tot_w / tot_s))
     out["speedup_bf16_vs_one_launch_per_image"] = (out["bf16"]["window_projections_per_s"] /
                                                    (tot_w / tot_s))
     return out
@@ -317,7 +330,7 @@ def bench_batched(smre, torch, stream, peak):
 def bench_mixed(smre, torch, stream, peak, threads):
     """One 2048 x 2048 residual (1600 emitters), window sides 1..12: FP32 vs
     BF16 vs FP16 increments with per-window scales; error against the FP64
-    oracle measured on a 256 x 256 crop with the same sides."""
+    oracle measured on the whole image after 3 cycles."""
     import oracle
     from synthetic import emitter_residual_2048
     sides = list(range(1, 13))
@@ -330,7 +343,7 @@ def bench_mixed(smre, torch, stream, peak, threads):
     cycles = 3
     res = {}
     for name, qdt in (("fp32", 0), ("bf16", 1), ("fp16", 2)):
-        sec, _ = timed_batch_cycles(smre, torch, [x], sides, cS, qdt, cycles, stream)
+        sec, _, _ = timed_batch_cycles(smre, torch, [x], sides, cS, qdt, cycles, stream)
         gbs = q_bytes_per_cycle(shapes, sides, qdt) / sec / 1e9
         out[name] = {"ms_per_cycle": 1e3 * sec, "window_projections_per_s": wpc / sec,
                      "achieved_gbs": gbs, "frac_of_measured_hbm": gbs / peak}
@@ -349,11 +362,17 @@ def bench_mixed(smre, torch, stream, peak, threads):
     return out
 
 
-def _serve(smre, stream, imgs, arrivals, kw, slots):
-    """The request loop on one arrival stream: images/s and latency quantiles
-    (submission to result, queueing included)."""
+def _quantiles(lat):
+    lat = sorted(lat)
+    return lat[len(lat) // 2], lat[min(len(lat) - 1, int(round(0.99 * (len(lat) - 1))))]
+
+
+def _serve(smre, stream, imgs, arrivals, kw, slots, qdt):
+    """The request loop on one arrival stream with increments of type qdt:
+    images/s and latency quantiles (submission to result, queueing included),
+    plus every request's result and cycle count."""
     outs = [np.empty_like(a) for a in imgs]
-    with smre.Server(SIDES, cycles_per_round=4, stream=stream, q_dtype=smre.SMRE_Q_BF16,
+    with smre.Server(SIDES, cycles_per_round=4, stream=stream, q_dtype=qdt,
                      max_images=slots, device_bytes=48 << 30, **kw) as S:
         t0 = time.perf_counter()
         tickets = []
@@ -362,40 +381,59 @@ def _serve(smre, stream, imgs, arrivals, kw, slots):
             if d > 0:
                 time.sleep(d)
             tickets.append(S.submit(img, o))
-        for t in tickets:
-            S.wait(t)
+        cycles = [S.wait(t).cycles for t in tickets]
         st = S.stats()
-    return {"images_per_s": st.images_per_s, "p50_s": st.p50_s, "p99_s": st.p99_s,
-            "max_s": st.max_s, "peak_active": st.peak_active, "rounds": st.rounds}
+    return ({"images_per_s": st.images_per_s, "p50_s": st.p50_s, "p99_s": st.p99_s,
+             "max_s": st.max_s, "peak_active": st.peak_active, "rounds": st.rounds}, outs, cycles)
 
 
 def _plain(smre, stream, imgs, arrivals, kw):
     """The plain single-image API (FP32) on the same stream, one request at a
-    time in arrival order."""
-    lat = []
+    time in arrival order.  A handle is created for each request but its
+    creation (device allocation of up to 3.4 GB of increments) is left out of
+    the timeline: the clock stops while it runs, so the latencies are those of
+    a plain server that had its handles ready.  The creation time is reported
+    beside them."""
+    lat, outs, cycles = [], [], []
     t0 = time.perf_counter()
+    t_create = 0.0
     for a, img in zip(arrivals, imgs):
-        d = t0 + a - time.perf_counter()
+        d = t0 + t_create + a - time.perf_counter()
         if d > 0:
             time.sleep(d)
         h, w = img.shape
-        with smre.Projector(h, w, SIDES, stream=stream, **kw) as P:
-            o = np.empty_like(img)
-            P.project(img, o)
-        lat.append(time.perf_counter() - t0 - a)
-    t_all = time.perf_counter() - t0
-    lat.sort()
-    return {"images_per_s": len(imgs) / t_all, "p50_s": lat[len(lat) // 2],
-            "p99_s": lat[min(len(lat) - 1, int(round(0.99 * (len(lat) - 1))))]}
+        c = time.perf_counter()
+        P = smre.Projector(h, w, SIDES, stream=stream, **kw)
+        t_create += time.perf_counter() - c
+        o = np.empty_like(img)
+        r = P.project(img, o)
+        lat.append(time.perf_counter() - t0 - t_create - a)
+        c = time.perf_counter()
+        P.close()
+        t_create += time.perf_counter() - c
+        outs.append(o)
+        cycles.append(r.cycles)
+    t_all = time.perf_counter() - t0 - t_create
+    p50, p99 = _quantiles(lat)
+    return ({"images_per_s": len(imgs) / t_all, "p50_s": p50, "p99_s": p99,
+             "handle_create_destroy_s_excluded": t_create}, outs, cycles)
 
 
-def bench_serving(smre, torch, stream, n_req=64, rate=500.0, slots=16, sweep=((5.0, 24), (15.0, 24))):
+def bench_serving(smre, torch, stream, threads, n_req=None, rate=500.0, slots=16,
+                  sweep=((5.0, 24), (15.0, 24))):
     """Poisson arrivals (mean `rate` per second) of square SOFI-like requests,
-    side uniform in 64..2048, window sides 1..8, BF16 increments, at most 100
-    cycles or a relative step of 1e-6: the request loop against the plain
-    single-image API (FP32, one request at a time, in arrival order) -- at
-    the overloading rate (saturation throughput) and at rates below it."""
+    side uniform in 64..2048, window sides 1..8, at most 100 cycles or a
+    relative step of 1e-6: the request loop with FP32 increments and with
+    BF16 increments against the plain single-image API (FP32, one request at
+    a time, in arrival order, handle creation left out of its timeline) -- at
+    the overloading rate (saturation throughput) and at rates below it.  Each
+    arm's error against the FP64 oracle is measured on the smallest requests
+    of the stream (the oracle run to each request's own cycle count).
+    n_req: SMRE_SERVING_REQUESTS, default 256."""
     from synthetic import request_stream, request_image, sofi_canvas
+    import oracle
+    if n_req is None:
+        n_req = int(os.environ.get("SMRE_SERVING_REQUESTS", "256"))
     canvas = sofi_canvas()
     cS = smre.smre_bounds(smre.make_params(64, 64, SIDES, alpha=ALPHA))
     kw = dict(cmode=smre.SMRE_C_EXPLICIT, c_explicit=cS, max_cycles=100, tol=1e-6,
@@ -408,17 +446,36 @@ def bench_serving(smre, torch, stream, n_req=64, rate=500.0, slots=16, sweep=((5
         return imgs, [a for (a, _, _) in reqs]
 
     imgs, arrivals = stream_of(n_req, rate)
-    served = _serve(smre, stream, imgs, arrivals, kw, slots)
-    plain = _plain(smre, stream, imgs, arrivals, kw)
+    arms = {}
+    results = {}
+    for name, fn in (("served_fp32", lambda: _serve(smre, stream, imgs, arrivals, kw, slots, 0)),
+                     ("served_bf16", lambda: _serve(smre, stream, imgs, arrivals, kw, slots, 1)),
+                     ("plain_single_image_fp32", lambda: _plain(smre, stream, imgs, arrivals, kw))):
+        arms[name], outs, cyc = fn()
+        results[name] = (outs, cyc)
+    # accuracy: the oracle on the smallest requests, to each arm's cycle count
+    sample = sorted(range(len(imgs)), key=lambda i: imgs[i].size)[:4]
+    for name, (outs, cyc) in results.items():
+        worst = 0.0
+        for i in sample:
+            ref = oracle.dykstra(imgs[i].astype(np.float64), SIDES, cS, max_cycles=cyc[i], tol=-1,
+                                 n_threads=threads).x
+            worst = max(worst, float(np.abs(outs[i].astype(np.float64) - ref).max() / np.abs(ref).max()))
+        arms[name]["err_vs_fp64_oracle"] = worst
+    arms["accuracy_sample"] = ("the 4 smallest requests (sides %s), max-abs relative, oracle run to "
+                               "the same cycle count" % [int(imgs[i].shape[0]) for i in sample])
     below = []
     for r, n in sweep:
         im, ar = stream_of(n, r)
-        below.append({"rate_per_s": r, "requests": n, "served_bf16": _serve(smre, stream, im, ar, kw, slots),
-                      "plain_single_image_fp32": _plain(smre, stream, im, ar, kw)})
+        below.append({"rate_per_s": r, "requests": n,
+                      "served_fp32": _serve(smre, stream, im, ar, kw, slots, 0)[0],
+                      "served_bf16": _serve(smre, stream, im, ar, kw, slots, 1)[0],
+                      "plain_single_image_fp32": _plain(smre, stream, im, ar, kw)[0]})
+    plain_ips = arms["plain_single_image_fp32"]["images_per_s"]
     return {"requests": n_req, "rate_per_s": rate, "sides": "1..8", "slots": slots,
-            "stop": "rel step < 1e-6 or 100 cycles", "served_bf16": served,
-            "plain_single_image_fp32": plain,
-            "images_per_s_ratio": served["images_per_s"] / plain["images_per_s"],
+            "stop": "rel step < 1e-6 or 100 cycles", **arms,
+            "images_per_s_ratio_fp32_served_vs_plain": arms["served_fp32"]["images_per_s"] / plain_ips,
+            "images_per_s_ratio_bf16_served_vs_plain": arms["served_bf16"]["images_per_s"] / plain_ips,
             "below_saturation": below}
 
 
@@ -493,7 +550,7 @@ def run_extras(smre, torch, stream, peak, threads):
     out = {}
     for name, fn in (("batched_256_uneven", lambda: bench_batched(smre, torch, stream, peak)),
                      ("mixed_precision_2048", lambda: bench_mixed(smre, torch, stream, peak, threads)),
-                     ("serving_poisson", lambda: bench_serving(smre, torch, stream)),
+                     ("serving_poisson", lambda: bench_serving(smre, torch, stream, threads)),
                      ("admm_512", lambda: bench_admm(smre, torch, stream, threads))):
         t = time.perf_counter()
         try:

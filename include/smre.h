@@ -288,8 +288,22 @@ typedef struct {
     int q_dtype;                /* SMRE_Q_FP32, SMRE_Q_BF16 or SMRE_Q_FP16          */
     int max_images;             /* slots, 1..65536                                  */
     size_t device_bytes;        /* arena for the images' state                      */
-    int flags;                  /* reserved, 0                                      */
+    int flags;                  /* SMRE_BF_* below                                  */
 } smre_batch_params;
+
+/* Batch flags.  A step launch's work list holds items of k consecutive
+ * window-rows of one image; k is at most the kernel's width over the image's
+ * row stride and at most ceil(window-rows of the step / (SMs x spread)), so
+ * the items of a step cover every SM `spread` times (more, smaller items
+ * balance better; fewer, longer ones refill the shared-memory ring less
+ * often).  The results do not depend on the spread, bit for bit. */
+#define SMRE_BF_AUTOTUNE 1        /* the first smre_batch_run of at least 4 cycles on a
+                                     set of image shapes times one cycle at each
+                                     spread 1, 2, 4 (after one untimed cycle) and keeps
+                                     the fastest; the choice is cached per (device,
+                                     shapes, sides, q_dtype) for the process        */
+#define SMRE_BF_SPREAD2 2         /* spread 2 (default 1)                           */
+#define SMRE_BF_SPREAD4 4         /* spread 4                                      */
 
 /* Arena bytes one height x width image takes under p (0: p invalid or the
  * image unsupported: width above 2048 or a side above min(height, width)). */
@@ -330,6 +344,11 @@ SMRE_API smre_status smre_batch_project(smre_batch *b, int n, const int *heights
 
 /* Images admitted and not yet retrieved. */
 SMRE_API int smre_batch_active(const smre_batch *b);
+
+/* The spread the batch's step launches use now (1, 2 or 4; see SMRE_BF_*),
+ * and in *tuned whether SMRE_BF_AUTOTUNE chose it (1 measured, 2 cached, 0
+ * not tuned); tuned may be NULL.  The paper has no counterpart. */
+SMRE_API int smre_batch_item_spread(const smre_batch *b, int *tuned);
 
 /* Kernels the batch has launched since it was created. */
 SMRE_API long long smre_batch_kernel_launches(const smre_batch *b);

@@ -25,6 +25,7 @@
 #include <cstring>
 #include <iterator>
 #include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -141,6 +142,12 @@ struct smre_batch {
     bool dirty = true;
     std::vector<int> step_items, step_prefix_at, step_kpack_at;
     int norm_chunks = 0, norm_prefix_at = 0;
+    // items of a step cover every SM `spread` times (SMRE_BF_*)
+    int spread = 1;
+    bool autotune = false;
+    int tuned = 0;                 // 1 measured, 2 cached, 0 not tuned
+    std::string tuned_key;         // the shapes the current spread was tuned for
+    cudaEvent_t tev0 = nullptr, tev1 = nullptr;
     long long launches = 0;
     // one cycle's launches captured in a CUDA graph, rebuilt when the item
     // tables or the stopping rule change
@@ -185,6 +192,10 @@ smre_status check_batch_params(const smre_batch_params *p, std::vector<int> &sid
         return bfail(nullptr, SMRE_EINVAL, "need 1..64 window sides");
     if (p->q_dtype < SMRE_Q_FP32 || p->q_dtype > SMRE_Q_FP16)
         return bfail(nullptr, SMRE_EINVAL, "q_dtype %d unknown", p->q_dtype);
+    if (p->flags & ~(SMRE_BF_AUTOTUNE | SMRE_BF_SPREAD2 | SMRE_BF_SPREAD4))
+        return bfail(nullptr, SMRE_EINVAL, "unknown batch flags 0x%x", p->flags);
+    if ((p->flags & SMRE_BF_SPREAD2) && (p->flags & SMRE_BF_SPREAD4))
+        return bfail(nullptr, SMRE_EINVAL, "SMRE_BF_SPREAD2 and SMRE_BF_SPREAD4 together");
     if (p->cmode != SMRE_C_PERSET && p->cmode != SMRE_C_CHI2 && p->cmode != SMRE_C_EXPLICIT)
         return bfail(nullptr, SMRE_EINVAL, "batches take cmode PERSET, CHI2 or EXPLICIT");
     if (p->cmode != SMRE_C_EXPLICIT && !(p->alpha > 0.0 && p->alpha < 1.0))
@@ -267,6 +278,24 @@ bool image_layout(const std::vector<int> &sides, int qtype, int hist_cap, int H,
     return true;
 }
 
+// Spreads chosen by SMRE_BF_AUTOTUNE, per (device, shapes, sides, q_dtype).
+std::mutex g_spread_mu;
+std::map<std::string, int> g_spread_cache;
+
+std::string spread_key(const smre_batch *b)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::vector<std::pair<int, int>> shapes;
+    for (int s : b->active) shapes.emplace_back(b->slots[s].H, b->slots[s].W);
+    std::sort(shapes.begin(), shapes.end());
+    std::string k = std::to_string(dev) + "|" + std::to_string(b->qtype) + "|";
+    for (int L : b->sides) k += std::to_string(L) + ",";
+    k += "|";
+    for (auto &sh : shapes) k += std::to_string(sh.first) + "x" + std::to_string(sh.second) + ",";
+    return k;
+}
+
 // Rebuild the item tables of the active images and upload them.
 smre_status rebuild_tables(smre_batch *b)
 {
@@ -286,7 +315,8 @@ smre_status rebuild_tables(smre_batch *b)
         // cover every SM (few or small images)
         long long total_units = 0;
         for (int i = 0; i < n; ++i) total_units += (b->slots[b->active[i]].H - st.a) / st.L;
-        const int kcap = (int)std::max(1LL, (total_units + b->sms - 1) / b->sms);
+        const long long lanes = (long long)b->sms * b->spread;
+        const int kcap = (int)std::max(1LL, (total_units + lanes - 1) / lanes);
         int acc = 0;
         std::vector<int> kp(n);
         for (int i = 0; i < n; ++i) {
@@ -393,6 +423,8 @@ void free_batch(smre_batch *b)
     if (b->stream) cudaStreamSynchronize(b->stream);
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    if (b->tev0) cudaEventDestroy(b->tev0);
+    if (b->tev1) cudaEventDestroy(b->tev1);
     cudaFree(b->arena);
     cudaFree(b->d_imgs);
     cudaFree(b->d_ctl);
@@ -432,6 +464,8 @@ smre_status smre_batch_create(const smre_batch_params *p, void *cuda_stream, smr
     b->sides = sides;
     for (size_t i = 0; i < sides.size(); ++i) b->cS_of[sides[i]] = cS[i];
     b->qtype = p->q_dtype;
+    b->spread = (p->flags & SMRE_BF_SPREAD4) ? 4 : (p->flags & SMRE_BF_SPREAD2) ? 2 : 1;
+    b->autotune = (p->flags & SMRE_BF_AUTOTUNE) != 0;
     b->max_cycles = p->max_cycles;
     b->tol = p->tol;
     b->tol_relative = p->tol_relative ? 1 : 0;
@@ -582,16 +616,21 @@ smre_status smre::batch_submit_ld(smre_batch *b, int height, int width, const fl
 
 extern "C" {
 
-smre_status smre_batch_run(smre_batch *b, int cycles)
+namespace {
+
+// Item tables and the cycle's graph up to date for the active images.
+smre_status prepare_cycle(smre_batch *b)
 {
-    if (!b) return bfail(nullptr, SMRE_EINVAL, "batch is NULL");
-    if (cycles < 0) return bfail(b, SMRE_EINVAL, "cycles is negative");
-    if (b->active.empty() || cycles == 0) return SMRE_OK;
     if (b->dirty) {
         smre_status st = rebuild_tables(b);
         if (st != SMRE_OK) return st;
     }
     if (b->graph_ok && b->graph_dirty) capture_cycle(b);
+    return SMRE_OK;
+}
+
+smre_status launch_cycles(smre_batch *b, int cycles)
+{
     for (int c = 0; c < cycles; ++c) {
         if (b->gexec) {
             BCK(b, cudaGraphLaunch(b->gexec, b->stream));
@@ -602,6 +641,90 @@ smre_status smre_batch_run(smre_batch *b, int cycles)
         }
     }
     return SMRE_OK;
+}
+
+void set_spread(smre_batch *b, int spread)
+{
+    if (b->spread != spread) {
+        b->spread = spread;
+        b->dirty = true;
+    }
+}
+
+// SMRE_BF_AUTOTUNE: pick the spread for the active set of shapes, from the
+// process-wide cache or by timing one cycle at each candidate (after one
+// untimed cycle: images that just joined read no increments in their first
+// cycle).  The cycles it runs are counted against `cycles`; the results do
+// not depend on the spread.
+smre_status tune_spread(smre_batch *b, int &cycles)
+{
+    const std::string key = spread_key(b);
+    if (key == b->tuned_key) return SMRE_OK;
+    {
+        std::lock_guard<std::mutex> lk(g_spread_mu);
+        auto it = g_spread_cache.find(key);
+        if (it != g_spread_cache.end()) {
+            set_spread(b, it->second);
+            b->tuned = 2;
+            b->tuned_key = key;
+            return SMRE_OK;
+        }
+    }
+    static const int kCand[] = {1, 2, 4};
+    if (cycles < 1 + (int)(sizeof(kCand) / sizeof(kCand[0]))) return SMRE_OK;   // tune later
+    smre_status st = prepare_cycle(b);
+    if (st == SMRE_OK) st = launch_cycles(b, 1);
+    if (st != SMRE_OK) return st;
+    --cycles;
+    if (!b->tev0) BCK(b, cudaEventCreate(&b->tev0));
+    if (!b->tev1) BCK(b, cudaEventCreate(&b->tev1));
+    int best = b->spread;
+    float best_ms = 1e30f;
+    for (int cand : kCand) {
+        set_spread(b, cand);
+        st = prepare_cycle(b);
+        if (st != SMRE_OK) return st;
+        BCK(b, cudaEventRecord(b->tev0, b->stream));
+        st = launch_cycles(b, 1);
+        if (st != SMRE_OK) return st;
+        BCK(b, cudaEventRecord(b->tev1, b->stream));
+        BCK(b, cudaEventSynchronize(b->tev1));
+        float ms = 0.f;
+        BCK(b, cudaEventElapsedTime(&ms, b->tev0, b->tev1));
+        --cycles;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = cand;
+        }
+    }
+    set_spread(b, best);
+    b->tuned = 1;
+    b->tuned_key = key;
+    std::lock_guard<std::mutex> lk(g_spread_mu);
+    g_spread_cache[key] = best;
+    return SMRE_OK;
+}
+
+}  // namespace
+
+smre_status smre_batch_run(smre_batch *b, int cycles)
+{
+    if (!b) return bfail(nullptr, SMRE_EINVAL, "batch is NULL");
+    if (cycles < 0) return bfail(b, SMRE_EINVAL, "cycles is negative");
+    if (b->active.empty() || cycles == 0) return SMRE_OK;
+    if (b->autotune) {
+        smre_status st = tune_spread(b, cycles);
+        if (st != SMRE_OK) return st;
+    }
+    smre_status st = prepare_cycle(b);
+    if (st != SMRE_OK) return st;
+    return launch_cycles(b, cycles);
+}
+
+int smre_batch_item_spread(const smre_batch *b, int *tuned)
+{
+    if (tuned) *tuned = b ? b->tuned : 0;
+    return b ? b->spread : 0;
 }
 
 smre_status smre_batch_poll(smre_batch *b, int *done, int max_done, int *n_done)

@@ -313,6 +313,41 @@ def test_autotuned_schedule_gives_the_same_answer(smre, torch_cuda, oracle_mod):
             assert P.schedule() == sched          # cached for the shape
 
 
+@pytest.mark.parametrize("qdt", [0, 1])
+def test_item_spread_and_its_autotuner_give_the_same_bits(smre, oracle_mod, qdt):
+    """Items of a step cover every SM `spread` times (1, 2 or 4); the per-window
+    arithmetic and the norm chunks do not depend on it, so every spread -- and
+    the one SMRE_BF_AUTOTUNE picks by timing cycles of the run itself -- gives
+    the same images bit for bit.  A second batch of the same shapes takes the
+    tuned spread from the cache."""
+    shapes = [(200, 300), (64, 64), (513, 257), (128, 1024), (90, 77)]
+    xs = images(shapes, seed0=901)
+    sides = [1, 2, 3, 5, 8]
+    cS = oracle_mod.bounds(sides, 0.9)
+    kw = dict(cmode=smre.SMRE_C_EXPLICIT, c_explicit=list(cS), max_cycles=9, tol=-1.0,
+              q_dtype=qdt, max_images=len(xs), device_bytes=1 << 30)
+    runs = {}
+    for name, flags in (("1", 0), ("2", smre.SMRE_BF_SPREAD2), ("4", smre.SMRE_BF_SPREAD4),
+                        ("tuned", smre.SMRE_BF_AUTOTUNE), ("cached", smre.SMRE_BF_AUTOTUNE)):
+        outs = [np.full_like(x, np.nan) for x in xs]
+        with smre.Batch(sides, flags=flags, **kw) as B:
+            slots = [B.submit(x) for x in xs]
+            assert all(sl >= 0 for sl in slots)
+            B.run(9)
+            done = B.poll()
+            assert sorted(done) == sorted(slots)
+            spread, tuned = B.item_spread()
+            for sl, o in zip(slots, outs):
+                B.retrieve(sl, o)
+        runs[name] = (outs, spread, tuned)
+    assert (runs["1"][1], runs["2"][1], runs["4"][1]) == (1, 2, 4)
+    assert runs["tuned"][2] in (1, 2) and runs["tuned"][1] in (1, 2, 4)
+    assert runs["cached"][2] == 2 and runs["cached"][1] == runs["tuned"][1]
+    for name in ("2", "4", "tuned", "cached"):
+        for a, b in zip(runs["1"][0], runs[name][0]):
+            assert np.array_equal(a, b), name
+
+
 # ------------------------------------------------------ full workload sizes
 
 def test_full_size_2048_sides_1_to_12(smre, oracle_mod):
@@ -336,6 +371,30 @@ def test_full_size_2048_sides_1_to_12(smre, oracle_mod):
         # cycle: sum_L L^2 = 650 here against 204 for sides 1..8
         bound = TOL if qdt == 0 else U16_ENVELOPE * U16[qdt] * np.sqrt(sum(L * L for L in sides) / 204.0)
         assert err(out, ref) <= bound, (qdt, err(out, ref))
+
+
+def test_full_size_2048_fp32_long_run(smre, oracle_mod):
+    """The 2048 x 2048 workload in FP32 over 100 cycles (650 set updates per
+    pixel per cycle, 65 000 in all) against the FP64 oracle at the same cycle
+    count: the FP32 rounding of the GPU must stay within the 1e-5 bar over
+    the long run too (Algorithm 2; the error is printed)."""
+    from synthetic import emitter_residual_2048
+    x0 = f32(emitter_residual_2048())
+    sides = list(range(1, 13))
+    cS = oracle_mod.bounds(sides, 0.9)
+    cycles = 100
+    out = np.empty_like(x0)
+    with smre.Projector(2048, 2048, sides, cmode=smre.SMRE_C_EXPLICIT, c_explicit=list(cS),
+                        max_cycles=cycles, tol=-1.0) as P:
+        r = P.project(x0, out)
+        hist = P.history()
+    assert r.cycles == cycles
+    ref = oracle_mod.dykstra(x0.astype(np.float64), sides, cS, max_cycles=cycles, tol=-1,
+                             n_threads=NTH)
+    e = err(out, ref.x)
+    print(f"2048x2048 sides 1..12, {cycles} FP32 cycles: err vs FP64 oracle {e:.3e}")
+    assert e <= TOL, e
+    assert np.allclose(hist, ref.hist, rtol=1e-4, atol=1e-6 * np.abs(ref.hist).max())
 
 
 def test_full_uneven_batch_sampled(smre, oracle_mod):

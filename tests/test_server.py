@@ -1,8 +1,9 @@
 """Continuous-batching request loop (smre_server_*).
 
 Requests of different sizes arrive from several threads while others are on
-the GPU; each result must equal, bit for bit, the same image projected alone,
-and the latency counters must account for every request.
+the GPU; each result must equal, bit for bit, the same image projected alone
+(with FP32 and with BF16 increments), and the latency counters must account
+for every request.
 """
 import threading
 import time
@@ -23,12 +24,13 @@ def smre():
     return m
 
 
-def test_served_results_equal_alone_and_counters(smre, oracle_mod):
+@pytest.mark.parametrize("q_dtype", [0, 1])      # FP32 and BF16 increments
+def test_served_results_equal_alone_and_counters(smre, oracle_mod, q_dtype):
     from synthetic import sofi_like
     sides = list(range(1, 6))
     cS = oracle_mod.bounds(sides, 0.9)
     kw = dict(cmode=smre.SMRE_C_EXPLICIT, c_explicit=list(cS), max_cycles=80, tol=1e-5,
-              tol_relative=True)
+              tol_relative=True, q_dtype=q_dtype)
     sizes = [64, 96, 130, 64, 200, 77, 128, 256, 90, 64, 150, 100]
     imgs = [np.ascontiguousarray(sofi_like(side=s, frames=40, seed=500 + i), np.float32)
             for i, s in enumerate(sizes)]
