@@ -87,6 +87,37 @@ struct QConv<__nv_bfloat16> {
         *reinterpret_cast<__nv_bfloat162 *>(p) = h;
         return __bfloat1622float2(h);
     }
+    // BF16 dequantisation takes the mixed-precision fma (FP32 result, BF16
+    // operands): the stored pair is used as it is, with no widening step.
+    // s packed as a bf16 pair (powers of two and zero convert exactly)
+    __device__ static unsigned pack(float2 s)
+    {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(s.x, s.y);
+        return *reinterpret_cast<const unsigned *>(&h);
+    }
+    // (h.x s.x + x.x, h.y s.y + x.y) with one rounding each, from the packed
+    // bf16 pairs h and s: the products are exact in FP32, so this equals the
+    // FP32 fma of the widened operands
+    __device__ static float2 fma_packed(unsigned h, unsigned s, float2 x)
+    {
+        float2 r;
+        asm("{\n\t.reg .b16 hl, hh, sl, sh;\n\t"
+            "mov.b32 {hl, hh}, %2;\n\tmov.b32 {sl, sh}, %3;\n\t"
+            "fma.rn.f32.bf16 %0, hl, sl, %4;\n\tfma.rn.f32.bf16 %1, hh, sh, %5;\n\t}"
+            : "=f"(r.x), "=f"(r.y) : "r"(h), "r"(s), "f"(x.x), "f"(x.y));
+        return r;
+    }
+    __device__ static float2 load_fma(const __nv_bfloat16 *p, float2, unsigned sb, float2 x)
+    {
+        return fma_packed(*reinterpret_cast<const unsigned *>(p), sb, x);
+    }
+    __device__ static float2 store_fma(__nv_bfloat16 *p, float2 v, float2, unsigned nswb, float2 y)
+    {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(v.x, v.y);
+        const unsigned hb = *reinterpret_cast<const unsigned *>(&h);
+        *reinterpret_cast<unsigned *>(p) = hb;
+        return fma_packed(hb, nswb, y);
+    }
 };
 template <>
 struct QConv<__half> {
@@ -100,6 +131,40 @@ struct QConv<__half> {
         const __half2 h = __floats2half2_rn(a, b);
         *reinterpret_cast<__half2 *>(p) = h;
         return __half22float2(h);
+    }
+};
+
+// Dequantising fma of the 16-bit types: y = h s + x and x = y - h sw from the
+// stored pair h.  Types with a packed form (QConv::pack) take the scales as a
+// packed pair as well; the others widen h and use the FP32x2 fma.
+template <typename C, typename = void>
+struct QFma {
+    static constexpr bool packed = false;
+    __device__ static unsigned pack(float2) { return 0u; }
+    template <typename QT>
+    __device__ static float2 load_fma(const QT *p, float2 s, unsigned, float2 x)
+    {
+        return __ffma2_rn(C::load2(p), s, x);
+    }
+    template <typename QT>
+    __device__ static float2 store_fma(QT *p, float2 v, float2 nsw, unsigned, float2 y)
+    {
+        return __ffma2_rn(C::store2(p, v.x, v.y), nsw, y);
+    }
+};
+template <typename C>
+struct QFma<C, decltype((void)C::pack(float2{}))> {
+    static constexpr bool packed = true;
+    __device__ static unsigned pack(float2 s) { return C::pack(s); }
+    template <typename QT>
+    __device__ static float2 load_fma(const QT *p, float2 s, unsigned sb, float2 x)
+    {
+        return C::load_fma(p, s, sb, x);
+    }
+    template <typename QT>
+    __device__ static float2 store_fma(QT *p, float2 v, float2 nsw, unsigned nswb, float2 y)
+    {
+        return C::store_fma(p, v, nsw, nswb, y);
     }
 };
 
@@ -430,6 +495,7 @@ template <typename QT, int LB, bool EXACT>
 __global__ void __launch_bounds__(kThreads, 1) bstep_kernel(const BStepArgs A)
 {
     using C = QConv<QT>;
+    using QF = QFma<C>;
     constexpr bool MIXED = C::mixed;
     constexpr int CPP = cpp_of(LB);
     constexpr int VW = vw_of(LB);
@@ -555,13 +621,18 @@ __global__ void __launch_bounds__(kThreads, 1) bstep_kernel(const BStepArgs A)
                     s2.x = on[j][0] ? sc[so[j] + vv[j]] : 0.f;
                     s2.y = on[j][1] ? sc[so[j] + w1[j]] : 0.f;
                 }
+                const unsigned s2b = QF::pack(s2);
                 float2 sq = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int i = 0; i < LB; ++i) {
                     if (i < L) {
                         if (!first) {
-                            const float2 qv = C::load2(qc + i * VW + 2 * kNC * j);
-                            x[i][j] = MIXED ? __ffma2_rn(qv, s2, x[i][j]) : __fadd2_rn(x[i][j], qv);
+                            if constexpr (MIXED) {
+                                x[i][j] = QF::load_fma(qc + i * VW + 2 * kNC * j, s2, s2b, x[i][j]);
+                            } else {
+                                const float2 qv = C::load2(qc + i * VW + 2 * kNC * j);
+                                x[i][j] = __fadd2_rn(x[i][j], qv);
+                            }
                         }
                         sq = __ffma2_rn(x[i][j], x[i][j], sq);
                     }
@@ -661,13 +732,14 @@ __global__ void __launch_bounds__(kThreads, 1) bstep_kernel(const BStepArgs A)
                     const float2 f2 = make_float2(WinData<MIXED>::f(wf[j][0]), WinData<MIXED>::f(wf[j][1]));
                     const float sw0 = WinData<MIXED>::sw(wf[j][0]), sw1 = WinData<MIXED>::sw(wf[j][1]);
                     const float2 nsw = make_float2(-sw0, -sw1);
+                    const unsigned nswb = QF::pack(nsw);
 #pragma unroll
                     for (int i = 0; i < LB; ++i)
                         if (i < L) {
                             const float2 y = x[i][j];
                             const float2 v = __fmul2_rn(y, f2);
-                            const float2 h = C::store2(qc + i * VW + 2 * kNC * j, v.x, v.y);
-                            x[i][j] = __ffma2_rn(h, nsw, y);   // consistent: x = y - deq(q_s)
+                            // consistent: x = y - deq(q_s)
+                            x[i][j] = QF::store_fma(qc + i * VW + 2 * kNC * j, v, nsw, nswb, y);
                         }
                     if (on[j][0] && rr[j] == 0) sc[so[j] + vv[j]] = sw0;
                     if (on[j][1] && r1[j] == 0) sc[so[j] + w1[j]] = sw1;
