@@ -151,6 +151,7 @@ class Clocks:
 # traffic as null until it is captured again.
 MEASURED_TRAFFIC = {
     "smre-gb300 0.8 (sm_103a)": (217.6e6, 433.1e6),
+    "smre-gb300 0.9 (sm_103a)": (217.6e6, 433.1e6),
 }
 
 # Warp instructions one incomplete projection of this workload executes
@@ -162,7 +163,40 @@ MEASURED_TRAFFIC = {
 # instructions per cycle at the measured clock.
 ICD_WARP_INSTRUCTIONS = {
     "smre-gb300 0.8 (sm_103a)": 21737554,
+    "smre-gb300 0.9 (sm_103a)": 21737554,
 }
+
+
+# DRAM traffic per cycle of the batched step kernels (all step launches of
+# one later cycle, one ncu capture each: profiles/bstep_kernel_uneven_batch.md),
+# per library version and workload: (bytes read, bytes written).  The writes
+# miss what each launch leaves dirty in L2 (ncu flushes caches between the
+# serialised launches), so the reads are the check against the algorithmic
+# bytes; both are reported.
+BATCH_TRAFFIC = {
+    "smre-gb300 0.9 (sm_103a)": {
+        ("uneven256", 0): (135.795e9, 133.457e9), ("uneven256", 1): (82.654e9, 80.306e9),
+        ("img2048", 0): (12.176e9, 7.194e9), ("img2048", 1): (6.949e9, 2.154e9),
+    },
+}
+
+
+def x_row_bytes_per_cycle(shapes, sides):
+    """x rows a cycle's step launches read and write: every group launch
+    (L, a) stages the rows of its window-rows, 8 bytes a pixel."""
+    return sum(8 * h * w * L for (h, w) in shapes for L in sides)
+
+
+def batch_traffic(smre, case, qdt, shapes, sides):
+    t = BATCH_TRAFFIC.get(smre.smre_version(), {}).get((case, qdt))
+    if t is None:
+        return None
+    inc = q_bytes_per_cycle(shapes, sides, qdt) - 8 * sum(h * w for h, w in shapes)
+    xr = x_row_bytes_per_cycle(shapes, sides)
+    return {"read": t[0], "write": t[1], "algorithmic_increments": inc, "algorithmic_x_rows": xr,
+            "read_over_algorithmic_read": t[0] / ((inc + xr) / 2),
+            "note": "all step launches of one later cycle; writes miss what stays dirty in L2 "
+                    "between the serialised launches"}
 
 
 def measured_peak_hbm():
@@ -302,7 +336,8 @@ def bench_batched(smre, torch, stream, peak):
         gbs = q_bytes_per_cycle(shapes, SIDES, qdt) / sec / 1e9
         out[name] = {"ms_per_cycle": 1e3 * sec, "window_projections_per_s": wpc / sec,
                      "achieved_gbs": gbs, "frac_of_measured_hbm": gbs / peak,
-                     "item_spread": spread, "spread_autotuned": {1: "measured", 2: "cached"}.get(tuned, "no")}
+                     "item_spread": spread, "spread_autotuned": {1: "measured", 2: "cached"}.get(tuned, "no"),
+                     "step_kernel_dram_traffic_per_cycle": batch_traffic(smre, "uneven256", qdt, shapes, SIDES)}
         # the untuned launches (spread 1) beside the tuned ones
         sec1, _, _ = timed_batch_cycles(smre, torch, xs, SIDES, cS, qdt, cycles, stream)
         out[name]["ms_per_cycle_spread1"] = 1e3 * sec1
@@ -324,6 +359,7 @@ def bench_batched(smre, torch, stream, peak):
                                                    (tot_w / tot_s))
     out["speedup_bf16_vs_one_launch_per_image"] = (out["bf16"]["window_projections_per_s"] /
                                                    (tot_w / tot_s))
+    out["bf16_over_fp32_ms_per_cycle"] = out["bf16"]["ms_per_cycle"] / out["fp32"]["ms_per_cycle"]
     return out
 
 
@@ -346,7 +382,9 @@ def bench_mixed(smre, torch, stream, peak, threads):
         sec, _, _ = timed_batch_cycles(smre, torch, [x], sides, cS, qdt, cycles, stream)
         gbs = q_bytes_per_cycle(shapes, sides, qdt) / sec / 1e9
         out[name] = {"ms_per_cycle": 1e3 * sec, "window_projections_per_s": wpc / sec,
-                     "achieved_gbs": gbs, "frac_of_measured_hbm": gbs / peak}
+                     "achieved_gbs": gbs, "frac_of_measured_hbm": gbs / peak,
+                     "step_kernel_dram_traffic_per_cycle": batch_traffic(smre, "img2048", qdt, shapes, sides)}
+    out["bf16_over_fp32_ms_per_cycle"] = out["bf16"]["ms_per_cycle"] / out["fp32"]["ms_per_cycle"]
     # accuracy: the whole image, 3 cycles, each storage type against the FP64 oracle
     ref = oracle.dykstra(x_h.astype(np.float64), sides, cS, max_cycles=3, tol=-1,
                          n_threads=threads).x

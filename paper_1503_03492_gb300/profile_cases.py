@@ -9,6 +9,8 @@
         a batch of copies of that image (one step-kernel launch per group);
     python -m paper_1503_03492_gb300.profile_cases uneven [--images 32] [--q bf16] [--cycles 2]
         the first images of the uneven 256-image batch (sides 128..1024, half 2:1);
+    python -m paper_1503_03492_gb300.profile_cases img2048 [--q bf16] [--cycles 2]
+        the 2048 x 2048 emitter residual with window sides 1..12 (batched path);
     python -m paper_1503_03492_gb300.profile_cases admm512 [--iters 3] [--cycles 20]
         the ADMM outer loop on the same image (PSF sigma 2, 20 TV steps per
         iteration, a fixed number of projection cycles per eps-step).
@@ -31,7 +33,7 @@ QTYPES = {"fp32": 0, "bf16": 1, "fp16": 2}
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["standard512", "icd512", "batch512", "uneven", "admm512"])
+    ap.add_argument("case", choices=["standard512", "icd512", "batch512", "uneven", "img2048", "admm512"])
     ap.add_argument("--iters", type=int, default=3)
     ap.add_argument("--cycles", type=int, default=None)
     ap.add_argument("--images", type=int, default=None)
@@ -40,7 +42,7 @@ def main(argv=None):
 
     import torch
     import paper_1503_03492_gb300 as smre
-    from synthetic import batch_images, emitter_residual
+    from synthetic import batch_images, emitter_residual, emitter_residual_2048
 
     torch.cuda.set_device(0)
     sides = list(range(1, 9))
@@ -70,6 +72,10 @@ def main(argv=None):
         return 0
     if a.case == "batch512":
         xs = [torch.from_numpy(x0).cuda() for _ in range(a.images or 8)]
+    elif a.case == "img2048":
+        sides = list(range(1, 13))
+        cS = smre.smre_bounds(smre.make_params(64, 64, sides))
+        xs = [torch.from_numpy(np.ascontiguousarray(emitter_residual_2048(), np.float32)).cuda()]
     else:
         xs = [torch.from_numpy(np.ascontiguousarray(x, np.float32)).cuda()
               for x in batch_images(256)[: a.images or 32]]
