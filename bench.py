@@ -287,23 +287,23 @@ def windows_per_cycle(shapes, sides):
     return sum((h - L + 1) * (w - L + 1) for (h, w) in shapes for L in sides)
 
 
-def timed_batch_cycles(smre, torch, xs, sides, cS, qdt, cycles, stream, tune=False):
+def timed_batch_cycles(smre, torch, xs, sides, cS, qdt, cycles, stream, tune=False, flags=0):
     """Per-cycle device time of a batch over xs (device tensors): the first
     cycle (no increments to read) runs untimed -- with tune, the autotuner's
-    cycles too (one untimed, one per candidate spread) -- then `cycles`
-    timed.  Returns (seconds per cycle, launches, (spread, tuned))."""
-    warm = 4 if tune else 1
+    cycles too (one untimed, one per candidate schedule) -- then `cycles`
+    timed.  Returns (seconds per cycle, launches, (spread, tuned, per_side))."""
+    warm = 5 if tune else 1
     need = sum(smre.smre_batch_image_bytes(smre.make_batch_params(sides, q_dtype=qdt,
                                                                   max_cycles=cycles + warm), *x.shape)
                for x in xs)
     with smre.Batch(sides, stream=stream, cmode=smre.SMRE_C_EXPLICIT, c_explicit=cS, q_dtype=qdt,
                     max_cycles=cycles + warm, tol=-1.0, max_images=len(xs),
                     device_bytes=need + (64 << 20),
-                    flags=smre.SMRE_BF_AUTOTUNE if tune else 0) as B:
+                    flags=(smre.SMRE_BF_AUTOTUNE if tune else 0) | flags) as B:
         for x in xs:
             assert B.submit(x) >= 0
         B.run(warm)
-        spread = B.item_spread()
+        spread = B.item_spread() + (B.per_side(),)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         B.run(cycles)
@@ -331,16 +331,20 @@ def bench_batched(smre, torch, stream, peak):
            "windows_per_cycle": wpc}
     cycles = 4
     for name, qdt in (("bf16", smre.SMRE_Q_BF16), ("fp32", smre.SMRE_Q_FP32)):
-        sec, _, (spread, tuned) = timed_batch_cycles(smre, torch, xs, SIDES, cS, qdt, cycles, stream,
-                                                     tune=True)
+        sec, _, (spread, tuned, per_side) = timed_batch_cycles(smre, torch, xs, SIDES, cS, qdt, cycles,
+                                                               stream, tune=True)
         gbs = q_bytes_per_cycle(shapes, SIDES, qdt) / sec / 1e9
         out[name] = {"ms_per_cycle": 1e3 * sec, "window_projections_per_s": wpc / sec,
                      "achieved_gbs": gbs, "frac_of_measured_hbm": gbs / peak,
-                     "item_spread": spread, "spread_autotuned": {1: "measured", 2: "cached"}.get(tuned, "no"),
+                     "item_spread": spread, "launches": "per side" if per_side else "per group",
+                     "schedule_autotuned": {1: "measured", 2: "cached"}.get(tuned, "no"),
                      "step_kernel_dram_traffic_per_cycle": batch_traffic(smre, "uneven256", qdt, shapes, SIDES)}
-        # the untuned launches (spread 1) beside the tuned ones
+        # the untuned schedules (spread 1) beside the tuned one
         sec1, _, _ = timed_batch_cycles(smre, torch, xs, SIDES, cS, qdt, cycles, stream)
-        out[name]["ms_per_cycle_spread1"] = 1e3 * sec1
+        secs, _, _ = timed_batch_cycles(smre, torch, xs, SIDES, cS, qdt, cycles, stream,
+                                        flags=smre.SMRE_BF_PER_SIDE)
+        out[name]["ms_per_cycle_per_group_spread1"] = 1e3 * sec1
+        out[name]["ms_per_cycle_per_side_spread1"] = 1e3 * secs
     # one launch per image (FP32 single-image API), on the first 24 images
     tot_w, tot_s = 0, 0.0
     for x in xs[:24]:
@@ -379,9 +383,17 @@ def bench_mixed(smre, torch, stream, peak, threads):
     cycles = 3
     res = {}
     for name, qdt in (("fp32", 0), ("bf16", 1), ("fp16", 2)):
-        sec, _, _ = timed_batch_cycles(smre, torch, [x], sides, cS, qdt, cycles, stream)
+        sec, _, (spread, tuned, per_side) = timed_batch_cycles(smre, torch, [x], sides, cS, qdt, cycles,
+                                                               stream, tune=True)
+        secg, _, _ = timed_batch_cycles(smre, torch, [x], sides, cS, qdt, cycles, stream)
+        secs, _, _ = timed_batch_cycles(smre, torch, [x], sides, cS, qdt, cycles, stream,
+                                        flags=smre.SMRE_BF_PER_SIDE)
         gbs = q_bytes_per_cycle(shapes, sides, qdt) / sec / 1e9
-        out[name] = {"ms_per_cycle": 1e3 * sec, "window_projections_per_s": wpc / sec,
+        out[name] = {"ms_per_cycle": 1e3 * sec, "item_spread": spread,
+                     "launches": "per side" if per_side else "per group",
+                     "ms_per_cycle_per_group_spread1": 1e3 * secg,
+                     "ms_per_cycle_per_side_spread1": 1e3 * secs,
+                     "window_projections_per_s": wpc / sec,
                      "achieved_gbs": gbs, "frac_of_measured_hbm": gbs / peak,
                      "step_kernel_dram_traffic_per_cycle": batch_traffic(smre, "img2048", qdt, shapes, sides)}
     out["bf16_over_fp32_ms_per_cycle"] = out["bf16"]["ms_per_cycle"] / out["fp32"]["ms_per_cycle"]

@@ -296,14 +296,22 @@ typedef struct {
  * row stride and at most ceil(window-rows of the step / (SMs x spread)), so
  * the items of a step cover every SM `spread` times (more, smaller items
  * balance better; fewer, longer ones refill the shared-memory ring less
- * often).  The results do not depend on the spread, bit for bit. */
-#define SMRE_BF_AUTOTUNE 1        /* the first smre_batch_run of at least 4 cycles on a
-                                     set of image shapes times one cycle at each
-                                     spread 1, 2, 4 (after one untimed cycle) and keeps
-                                     the fastest; the choice is cached per (device,
-                                     shapes, sides, q_dtype) for the process        */
+ * often).  By default each group (L, a) of the cycle (Sec. 3.1: the tilings
+ * of one side and row offset) is one launch, so a group starts when the
+ * previous one has ended everywhere.  With SMRE_BF_PER_SIDE the L groups of a
+ * side share one cooperative launch: an item starts as soon as the items of
+ * the previous group of its image that share its rows have written them back
+ * (per-image window-row flags), so the tail of one group overlaps the next.
+ * The results depend on neither choice, bit for bit. */
+#define SMRE_BF_AUTOTUNE 1        /* the first smre_batch_run of at least 5 cycles on a
+                                     set of image shapes times one cycle of each of
+                                     spread 1 and 4, one launch per group and per side
+                                     (after one untimed cycle), and keeps the fastest;
+                                     the choice is cached per (device, shapes, sides,
+                                     q_dtype) for the process                       */
 #define SMRE_BF_SPREAD2 2         /* spread 2 (default 1)                           */
 #define SMRE_BF_SPREAD4 4         /* spread 4                                      */
+#define SMRE_BF_PER_SIDE 8        /* one cooperative launch per side               */
 
 /* Arena bytes one height x width image takes under p (0: p invalid or the
  * image unsupported: width above 2048 or a side above min(height, width)). */
@@ -349,6 +357,11 @@ SMRE_API int smre_batch_active(const smre_batch *b);
  * and in *tuned whether SMRE_BF_AUTOTUNE chose it (1 measured, 2 cached, 0
  * not tuned); tuned may be NULL.  The paper has no counterpart. */
 SMRE_API int smre_batch_item_spread(const smre_batch *b, int *tuned);
+
+/* 1 when the batch's step launches run one per side (SMRE_BF_PER_SIDE, or
+ * chosen by SMRE_BF_AUTOTUNE), 0 when one per group.  The paper has no
+ * counterpart. */
+SMRE_API int smre_batch_per_side(const smre_batch *b);
 
 /* Kernels the batch has launched since it was created. */
 SMRE_API long long smre_batch_kernel_launches(const smre_batch *b);

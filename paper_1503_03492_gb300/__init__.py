@@ -32,6 +32,7 @@ __all__ = [
     "smre_batch_image_bytes", "smre_batch_create", "smre_batch_submit", "smre_batch_run",
     "smre_batch_poll", "smre_batch_retrieve", "smre_batch_project", "smre_batch_active",
     "smre_batch_item_spread", "SMRE_BF_AUTOTUNE", "SMRE_BF_SPREAD2", "SMRE_BF_SPREAD4",
+    "SMRE_BF_PER_SIDE", "smre_batch_per_side",
     "smre_batch_kernel_launches", "smre_batch_device_bytes", "smre_batch_last_error",
     "smre_batch_destroy", "Batch", "smre_server_params", "smre_server_counters",
     "smre_server_create", "smre_server_submit", "smre_server_wait", "smre_server_stats",
@@ -49,7 +50,7 @@ SMRE_F_AUTOTUNE = 8
 SMRE_F_BAND_IN_SMEM = 16
 SMRE_SCHED_PERSISTENT, SMRE_SCHED_BATCHED, SMRE_SCHED_GROUPS = 1, 2, 3
 SMRE_Q_FP32, SMRE_Q_BF16, SMRE_Q_FP16 = range(3)
-SMRE_BF_AUTOTUNE, SMRE_BF_SPREAD2, SMRE_BF_SPREAD4 = 1, 2, 4
+SMRE_BF_AUTOTUNE, SMRE_BF_SPREAD2, SMRE_BF_SPREAD4, SMRE_BF_PER_SIDE = 1, 2, 4, 8
 
 _STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENOTCONVERGED"}
 
@@ -62,7 +63,8 @@ EXPORTED = (
     "smre_dykstra_project_static", "smre_dykstra_schedule", "smre_batch_image_bytes",
     "smre_batch_create",
     "smre_batch_submit", "smre_batch_run", "smre_batch_poll", "smre_batch_retrieve",
-    "smre_batch_project", "smre_batch_active", "smre_batch_item_spread", "smre_batch_kernel_launches",
+    "smre_batch_project", "smre_batch_active", "smre_batch_item_spread", "smre_batch_per_side",
+    "smre_batch_kernel_launches",
     "smre_batch_device_bytes", "smre_batch_last_error", "smre_batch_destroy",
     "smre_server_create", "smre_server_submit", "smre_server_wait", "smre_server_stats",
     "smre_server_destroy", "smre_admm_create", "smre_admm_solve", "smre_admm_kernel_launches",
@@ -195,6 +197,7 @@ def load():
                                     P(ctypes.c_void_p), P(ctypes.c_void_p), P(smre_result)]),
         "smre_batch_active": (ctypes.c_int, [H]),
         "smre_batch_item_spread": (ctypes.c_int, [H, P(ctypes.c_int)]),
+        "smre_batch_per_side": (ctypes.c_int, [H]),
         "smre_batch_kernel_launches": (ctypes.c_longlong, [H]),
         "smre_batch_device_bytes": (ctypes.c_size_t, [H]),
         "smre_batch_last_error": (ctypes.c_char_p, [H]),
@@ -531,6 +534,12 @@ def smre_batch_item_spread(b):
     return v, int(t.value)
 
 
+def smre_batch_per_side(b) -> bool:
+    """True when the batch's step launches run one per side (SMRE_BF_PER_SIDE
+    or chosen by SMRE_BF_AUTOTUNE)."""
+    return bool(load().smre_batch_per_side(b))
+
+
 def smre_batch_kernel_launches(b) -> int:
     return int(load().smre_batch_kernel_launches(b))
 
@@ -578,6 +587,9 @@ class Batch:
 
     def item_spread(self):
         return smre_batch_item_spread(self.b)
+
+    def per_side(self):
+        return smre_batch_per_side(self.b)
 
     def kernel_launches(self):
         return smre_batch_kernel_launches(self.b)

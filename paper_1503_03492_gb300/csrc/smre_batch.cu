@@ -119,7 +119,7 @@ cudaError_t batch_prepare(int qtype, size_t smem_max)
 
 cudaError_t launch_batch_step(int qtype, const BStepArgs &A, int grid, size_t smem, cudaStream_t s)
 {
-    if (A.n_items <= 0 || grid <= 0) return cudaSuccess;
+    if (A.max_items <= 0 || grid <= 0) return cudaSuccess;
     if (qtype == 1) return launch_batch_step_bf16(A, grid, smem, s);
     if (qtype == 2) return launch_batch_step_f16(A, grid, smem, s);
     return launch_batch_step_f32(A, grid, smem, s);

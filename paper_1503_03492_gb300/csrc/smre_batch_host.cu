@@ -90,7 +90,7 @@ private:
 // Where an H x W image's state sits inside its arena piece.
 struct Layout {
     int pitch = 0, nchunks = 0;
-    size_t x = 0, xprev = 0, q = 0, qs = 0, qoff = 0, soff = 0, hist = 0, part = 0, total = 0;
+    size_t x = 0, xprev = 0, q = 0, qs = 0, qoff = 0, soff = 0, hist = 0, part = 0, uflag = 0, total = 0;
     std::vector<long long> qoff_tab, soff_tab;   // per plane, cycle order
     long long windows_per_cycle = 0;
 };
@@ -127,6 +127,8 @@ struct smre_batch {
     int *h_err = nullptr;      // pinned
     int *d_tab = nullptr;      // item tables
     size_t tab_ints = 0;
+    BGroup *d_groups = nullptr;   // [steps] group descriptors into d_tab
+    bool per_side = false;        // one cooperative launch per side instead of per group
     unsigned long long timeout_ns = 10000000000ull;
     // host state
     struct Slot {
@@ -192,7 +194,7 @@ smre_status check_batch_params(const smre_batch_params *p, std::vector<int> &sid
         return bfail(nullptr, SMRE_EINVAL, "need 1..64 window sides");
     if (p->q_dtype < SMRE_Q_FP32 || p->q_dtype > SMRE_Q_FP16)
         return bfail(nullptr, SMRE_EINVAL, "q_dtype %d unknown", p->q_dtype);
-    if (p->flags & ~(SMRE_BF_AUTOTUNE | SMRE_BF_SPREAD2 | SMRE_BF_SPREAD4))
+    if (p->flags & ~(SMRE_BF_AUTOTUNE | SMRE_BF_SPREAD2 | SMRE_BF_SPREAD4 | SMRE_BF_PER_SIDE))
         return bfail(nullptr, SMRE_EINVAL, "unknown batch flags 0x%x", p->flags);
     if ((p->flags & SMRE_BF_SPREAD2) && (p->flags & SMRE_BF_SPREAD4))
         return bfail(nullptr, SMRE_EINVAL, "SMRE_BF_SPREAD2 and SMRE_BF_SPREAD4 together");
@@ -274,6 +276,7 @@ bool image_layout(const std::vector<int> &sides, int qtype, int hist_cap, int H,
     lo.soff = o;   o += align256(sizeof(long long) * np);
     lo.hist = o;   o += align256(sizeof(double) * 2 * (size_t)hist_cap);
     lo.part = o;   o += align256(sizeof(double) * 2 * (size_t)lo.nchunks);
+    lo.uflag = o;  o += align256(sizeof(unsigned) * (size_t)H);
     lo.total = o;
     return true;
 }
@@ -332,6 +335,10 @@ smre_status rebuild_tables(smre_batch *b)
         b->step_kpack_at[s] = (int)tab.size();
         tab.insert(tab.end(), kp.begin(), kp.end());
     }
+    std::vector<BGroup> groups(b->steps.size());
+    for (size_t s = 0; s < b->steps.size(); ++s)
+        groups[s] = BGroup{b->d_tab + b->step_prefix_at[s], b->d_tab + b->step_kpack_at[s],
+                           b->step_items[s], b->steps[s].a, b->steps[s].p0, (int)s};
     b->norm_prefix_at = (int)tab.size();
     int acc = 0;
     for (int i = 0; i < n; ++i) {
@@ -343,30 +350,41 @@ smre_status rebuild_tables(smre_batch *b)
     if (tab.size() > b->tab_ints) return bfail(b, SMRE_EINVAL, "item table overflow");
     BCK(b, cudaMemcpyAsync(b->d_tab, tab.data(), sizeof(int) * tab.size(), cudaMemcpyHostToDevice,
                            b->stream));
+    BCK(b, cudaMemcpyAsync(b->d_groups, groups.data(), sizeof(BGroup) * groups.size(),
+                           cudaMemcpyHostToDevice, b->stream));
     b->dirty = false;
     b->graph_dirty = true;
     return SMRE_OK;
 }
 
-// The launches of one cycle: one step kernel per group with items, then the
-// norm and the stopping test.
+// The launches of one cycle: the step kernel once per group with items (or
+// once per side, every group of the side in one cooperative launch), then
+// the norm and the stopping test.
 smre_status enqueue_cycle(smre_batch *b, cudaStream_t stream)
 {
     const int n = (int)b->active.size();
     int kernels = 0;
-    for (size_t s = 0; s < b->steps.size(); ++s) {
-        if (b->step_items[s] == 0) continue;
+    for (size_t s = 0; s < b->steps.size();) {
+        // groups s .. e - 1 go into one launch: one group, or every group of
+        // the side (consecutive offsets a = 0 .. L - 1, each waiting for the
+        // one before it)
+        size_t e = s + 1;
+        if (b->per_side)
+            while (e < b->steps.size() && b->steps[e].L == b->steps[s].L) ++e;
+        int max_items = 0;
+        for (size_t k = s; k < e; ++k) max_items = std::max(max_items, b->step_items[k]);
         const Step &st = b->steps[s];
+        const size_t first = s;
+        s = e;
+        if (max_items == 0) continue;
         BStepArgs A{};
         A.imgs = b->d_imgs;
         A.active = b->d_tab;
-        A.prefix = b->d_tab + b->step_prefix_at[s];
-        A.kpack = b->d_tab + b->step_kpack_at[s];
+        A.groups = b->d_groups + first;
         A.n_active = n;
-        A.n_items = b->step_items[s];
+        A.n_groups = (int)(e - first);
+        A.max_items = max_items;
         A.L = st.L;
-        A.a = st.a;
-        A.p0 = st.p0;
         A.cS = (float)b->cS_of[st.L];
         A.sqrt_cS = (float)std::sqrt(b->cS_of[st.L]);
         A.cS64 = b->cS_of[st.L];
@@ -374,7 +392,7 @@ smre_status enqueue_cycle(smre_batch *b, cudaStream_t stream)
         A.ring_bytes = (int)(b->smem - A.ring_offset);
         A.timeout_ns = b->timeout_ns;
         A.err = b->d_err;
-        const int grid = std::min(A.n_items, b->sms);
+        const int grid = std::min(A.max_items, b->sms);
         BCK(b, launch_batch_step(b->qtype, A, grid, b->smem, stream));
         ++kernels;
     }
@@ -430,6 +448,7 @@ void free_batch(smre_batch *b)
     cudaFree(b->d_ctl);
     cudaFree(b->d_err);
     cudaFree(b->d_tab);
+    cudaFree(b->d_groups);
     cudaFreeHost(b->h_ctl);
     cudaFreeHost(b->h_err);
     delete b;
@@ -466,6 +485,7 @@ smre_status smre_batch_create(const smre_batch_params *p, void *cuda_stream, smr
     b->qtype = p->q_dtype;
     b->spread = (p->flags & SMRE_BF_SPREAD4) ? 4 : (p->flags & SMRE_BF_SPREAD2) ? 2 : 1;
     b->autotune = (p->flags & SMRE_BF_AUTOTUNE) != 0;
+    b->per_side = (p->flags & SMRE_BF_PER_SIDE) != 0;
     b->max_cycles = p->max_cycles;
     b->tol = p->tol;
     b->tol_relative = p->tol_relative ? 1 : 0;
@@ -527,6 +547,7 @@ smre_status smre_batch_create(const smre_batch_params *p, void *cuda_stream, smr
     b->tab_ints = (size_t)b->max_images + b->steps.size() * (2 * (size_t)b->max_images + 1) +
                   (size_t)b->max_images + 1;
     CREATE_CK(dev_malloc(&b->d_tab, sizeof(int) * b->tab_ints));
+    CREATE_CK(dev_malloc(&b->d_groups, sizeof(BGroup) * b->steps.size()));
     CREATE_CK(host_malloc(&b->h_ctl, sizeof(Control) * b->max_images));
     CREATE_CK(host_malloc(&b->h_err, sizeof(int)));
     CREATE_CK(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
@@ -573,6 +594,7 @@ smre_status smre::batch_submit_ld(smre_batch *b, int height, int width, const fl
     im.ctl = b->d_ctl + s;
     im.hist = reinterpret_cast<double *>(base + lo.hist);
     im.part = reinterpret_cast<double *>(base + lo.part);
+    im.uflag = reinterpret_cast<unsigned *>(base + lo.uflag);
     im.H = height;
     im.W = width;
     im.pitch = lo.pitch;
@@ -598,6 +620,7 @@ smre_status smre::batch_submit_ld(smre_batch *b, int height, int width, const fl
     SUB_CK(cudaMemcpy2DAsync(im.xprev, sizeof(float) * lo.pitch, im.x, sizeof(float) * lo.pitch,
                              sizeof(float) * width, height, cudaMemcpyDeviceToDevice, b->stream));
     SUB_CK(cudaMemsetAsync(b->d_ctl + s, 0, sizeof(Control), b->stream));
+    SUB_CK(cudaMemsetAsync(im.uflag, 0, sizeof(unsigned) * (size_t)height, b->stream));
 #undef SUB_CK
     sl.used = true;
     sl.done = false;
@@ -651,11 +674,26 @@ void set_spread(smre_batch *b, int spread)
     }
 }
 
-// SMRE_BF_AUTOTUNE: pick the spread for the active set of shapes, from the
-// process-wide cache or by timing one cycle at each candidate (after one
-// untimed cycle: images that just joined read no increments in their first
-// cycle).  The cycles it runs are counted against `cycles`; the results do
-// not depend on the spread.
+void set_per_side(smre_batch *b, bool per_side)
+{
+    if (b->per_side != per_side) {
+        b->per_side = per_side;
+        b->graph_dirty = true;
+    }
+}
+
+// A schedule as cached: the spread, plus 256 for one launch per side.
+void set_schedule(smre_batch *b, int code)
+{
+    set_spread(b, code & 255);
+    set_per_side(b, (code & 256) != 0);
+}
+
+// SMRE_BF_AUTOTUNE: pick the schedule (one launch per group or per side) and
+// the spread for the active set of shapes, from the process-wide cache or by
+// timing one cycle of each candidate (after one untimed cycle: images that
+// just joined read no increments in their first cycle).  The cycles it runs
+// are counted against `cycles`; the results do not depend on the schedule.
 smre_status tune_spread(smre_batch *b, int &cycles)
 {
     const std::string key = spread_key(b);
@@ -664,13 +702,13 @@ smre_status tune_spread(smre_batch *b, int &cycles)
         std::lock_guard<std::mutex> lk(g_spread_mu);
         auto it = g_spread_cache.find(key);
         if (it != g_spread_cache.end()) {
-            set_spread(b, it->second);
+            set_schedule(b, it->second);
             b->tuned = 2;
             b->tuned_key = key;
             return SMRE_OK;
         }
     }
-    static const int kCand[] = {1, 2, 4};
+    static const int kCand[] = {1, 4, 256 | 1, 256 | 4};
     if (cycles < 1 + (int)(sizeof(kCand) / sizeof(kCand[0]))) return SMRE_OK;   // tune later
     smre_status st = prepare_cycle(b);
     if (st == SMRE_OK) st = launch_cycles(b, 1);
@@ -678,10 +716,10 @@ smre_status tune_spread(smre_batch *b, int &cycles)
     --cycles;
     if (!b->tev0) BCK(b, cudaEventCreate(&b->tev0));
     if (!b->tev1) BCK(b, cudaEventCreate(&b->tev1));
-    int best = b->spread;
+    int best = b->spread | (b->per_side ? 256 : 0);
     float best_ms = 1e30f;
     for (int cand : kCand) {
-        set_spread(b, cand);
+        set_schedule(b, cand);
         st = prepare_cycle(b);
         if (st != SMRE_OK) return st;
         BCK(b, cudaEventRecord(b->tev0, b->stream));
@@ -697,7 +735,7 @@ smre_status tune_spread(smre_batch *b, int &cycles)
             best = cand;
         }
     }
-    set_spread(b, best);
+    set_schedule(b, best);
     b->tuned = 1;
     b->tuned_key = key;
     std::lock_guard<std::mutex> lk(g_spread_mu);
@@ -726,6 +764,8 @@ int smre_batch_item_spread(const smre_batch *b, int *tuned)
     if (tuned) *tuned = b ? b->tuned : 0;
     return b ? b->spread : 0;
 }
+
+int smre_batch_per_side(const smre_batch *b) { return b && b->per_side ? 1 : 0; }
 
 smre_status smre_batch_poll(smre_batch *b, int *done, int max_done, int *n_done)
 {

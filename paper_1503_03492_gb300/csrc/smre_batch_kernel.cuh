@@ -188,8 +188,11 @@ struct BItem {
 // item's x chunk (so the consumers never wait on the item tables in HBM);
 // P < 0 marks the end of the CTA's items.
 struct ChunkInfo {
-    float *xrow;   // the item's first image row (x)
+    float *xrow;      // the item's first image row (x)
+    unsigned *uflag;  // the image's window-row flags
     int P, W, nu, first;
+    int u0;           // the item's first window-row
+    unsigned tag;     // what its flags get once its rows are back in HBM
 };
 
 // 2^(k + shift) for the smallest k with v <= 2^k (exponent k in ex), read from
@@ -271,14 +274,14 @@ __device__ __forceinline__ int find_active(const int *prefix, int n_active, int 
     return lo;
 }
 
-__device__ __forceinline__ BItem decode_item(const BStepArgs &A, int item)
+__device__ __forceinline__ BItem decode_item(const BStepArgs &A, const BGroup &G, int item)
 {
-    const int i = find_active(A.prefix, A.n_active, item);
+    const int i = find_active(G.prefix, A.n_active, item);
     BItem it;
     it.slot = __ldg(A.active + i);
-    const int k = __ldg(A.kpack + i);
-    const int units = (A.imgs[it.slot].H - A.a) / A.L;
-    it.u0 = (item - __ldg(A.prefix + i)) * k;
+    const int k = __ldg(G.kpack + i);
+    const int units = (A.imgs[it.slot].H - G.a) / A.L;
+    it.u0 = (item - __ldg(G.prefix + i)) * k;
     it.nu = min(k, units - it.u0);
     return it;
 }
@@ -301,6 +304,50 @@ __device__ inline bool wait_phase(uint64_t *bar, unsigned parity, const BStepArg
     }
     *s_abort = 1;
     return false;
+}
+
+// Flag tag of group G in the cycle of an image: grows with every group run,
+// so a flag at or above a group's tag says that group (or a later one) wrote
+// the window-row back.
+__device__ __forceinline__ unsigned group_tag(const BImage &im, const BGroup &G)
+{
+    return (unsigned)im.ctl->cycles * 256u + (unsigned)G.seq + 1u;
+}
+
+// Producer warp, several groups per launch: before an item's rows of x are
+// loaded, the previous group's window-rows v0..v1 of the image (those that
+// share rows with the item) must be back in HBM.  Lane k watches rows v0 + k,
+// v0 + k + 32, ... (one round trip when they are done already).  Bounded: on
+// expiry (or when another role gave up) it records the time-out, raises the
+// abort flag and returns false, in every lane.
+static __device__ __noinline__ bool wait_rows(const BStepArgs &A, const unsigned *uflag, int v0, int v1,
+                                              unsigned tag, volatile int *s_abort)
+{
+    const int lane = threadIdx.x & 31;
+    unsigned long long t0 = 0;
+    for (int base = v0; base <= v1; base += 32) {
+        const int v = base + lane;
+        for (;;) {
+            const bool ok = v > v1 || (int)(ld_acquire(uflag + v) - tag) >= 0;
+            if (__all_sync(0xffffffffu, ok)) break;
+            int give_up = 0;
+            if (lane == 0) {
+                const unsigned long long t = globaltimer();
+                if (*s_abort || ld_volatile(A.err)) {
+                    give_up = 1;
+                } else if (t0 == 0) {
+                    t0 = t;
+                } else if (t - t0 > A.timeout_ns) {
+                    atomicCAS(A.err, 0, (int)SMRE_ETIMEOUT);
+                    give_up = 1;
+                }
+                if (give_up) *s_abort = 1;
+            }
+            if (__shfl_sync(0xffffffffu, give_up, 0)) return false;
+            __nanosleep(100);
+        }
+    }
+    return true;
 }
 
 // Chunks in the ring have a fixed row stride: row i of an item's block sits at
@@ -381,48 +428,62 @@ __device__ void produce(const BStepArgs &A, unsigned char *ring, uint64_t *full,
         return ok != 0;
     };
 
-    for (int item = blockIdx.x; item < A.n_items && !dead; item += gridDim.x) {
-        const BItem it = decode_item(A, item);
-        const BImage im = A.imgs[it.slot];
-        if (im.ctl->stop) continue;
-        const int P = im.pitch;
-        const bool first = im.ctl->cycles == 0;
-        const int rows = it.nu * L;   // row r = unit r / L, row r % L of it
-        float *xsrc = im.x + (size_t)(A.a + L * it.u0) * P;
-        const ChunkInfo info{xsrc, P, im.W, it.nu, first ? 1 : 0};
-        int at, d;
-        if (!begin(L * VW * 4, (unsigned)(rows * P) * 4u, at, d, &info)) {
-            dead = true;
-            break;
-        }
-        for (int r = lane; r < rows; r += 32) {
-            const int s = r / L, i = r - s * L;
-            bulk_load(ring + at + (size_t)(i * VW + s * P) * 4, xsrc + (size_t)r * P,
-                      (unsigned)P * 4u, &full[d]);
-        }
-        const int nwp = scale_row(im.W, L);
-        const unsigned tx = first ? 0u
-                                  : (unsigned)(rows * P * esz) + (MIXED ? (unsigned)(it.nu * nwp) * 4u : 0u);
-        for (int b = 0; b < L; ++b) {
-            if (!begin(L * VW * esz + (MIXED ? VW * 4 : 0), tx, at, d, nullptr)) {
+    for (int g = 0; g < A.n_groups && !dead; ++g) {
+        const BGroup G = A.groups[g];
+        for (int item = blockIdx.x; item < G.n_items && !dead; item += gridDim.x) {
+            const BItem it = decode_item(A, G, item);
+            const BImage im = A.imgs[it.slot];
+            if (im.ctl->stop) continue;
+            const int P = im.pitch;
+            const bool first = im.ctl->cycles == 0;
+            const int rows = it.nu * L;   // row r = unit r / L, row r % L of it
+            float *xsrc = im.x + (size_t)(G.a + L * it.u0) * P;
+            const unsigned tag = group_tag(im, G);
+            if (g > 0) {
+                // group (L, a - 1) ran before in this launch: its window-rows
+                // u0 .. u0 + nu hold this item's rows
+                const int v1 = min(it.u0 + it.nu, (im.H - (G.a - 1)) / L - 1);
+                if (!wait_rows(A, im.uflag, it.u0, v1, tag - 1u, s_abort)) {
+                    dead = true;
+                    break;
+                }
+                fence_proxy_async_global();   // the rows written by other CTAs, for the bulk loads
+            }
+            const ChunkInfo info{xsrc, im.uflag, P, im.W, it.nu, first ? 1 : 0, it.u0, tag};
+            int at, d;
+            if (!begin(L * VW * 4, (unsigned)(rows * P) * 4u, at, d, &info)) {
                 dead = true;
                 break;
             }
-            if (first) continue;
-            const QT *qsrc = reinterpret_cast<const QT *>(im.q) + im.qoff[A.p0 + b] +
-                             (size_t)it.u0 * L * P;
             for (int r = lane; r < rows; r += 32) {
                 const int s = r / L, i = r - s * L;
-                bulk_load(ring + at + (size_t)(i * VW + s * P) * esz, qsrc + (size_t)r * P,
-                          (unsigned)(P * esz), &full[d]);
+                bulk_load(ring + at + (size_t)(i * VW + s * P) * 4, xsrc + (size_t)r * P,
+                          (unsigned)P * 4u, &full[d]);
             }
-            if (MIXED && lane == 0)
-                bulk_load(ring + at + (size_t)L * VW * esz, im.qs + im.soff[A.p0 + b] + (size_t)it.u0 * nwp,
-                          (unsigned)(it.nu * nwp) * 4u, &full[d]);
+            const int nwp = scale_row(im.W, L);
+            const unsigned tx = first ? 0u
+                                      : (unsigned)(rows * P * esz) + (MIXED ? (unsigned)(it.nu * nwp) * 4u : 0u);
+            for (int b = 0; b < L; ++b) {
+                if (!begin(L * VW * esz + (MIXED ? VW * 4 : 0), tx, at, d, nullptr)) {
+                    dead = true;
+                    break;
+                }
+                if (first) continue;
+                const QT *qsrc = reinterpret_cast<const QT *>(im.q) + im.qoff[G.p0 + b] +
+                                 (size_t)it.u0 * L * P;
+                for (int r = lane; r < rows; r += 32) {
+                    const int s = r / L, i = r - s * L;
+                    bulk_load(ring + at + (size_t)(i * VW + s * P) * esz, qsrc + (size_t)r * P,
+                              (unsigned)(P * esz), &full[d]);
+                }
+                if (MIXED && lane == 0)
+                    bulk_load(ring + at + (size_t)L * VW * esz, im.qs + im.soff[G.p0 + b] + (size_t)it.u0 * nwp,
+                              (unsigned)(it.nu * nwp) * 4u, &full[d]);
+            }
         }
     }
     if (!dead) {   // the end marker: a chunk without data
-        const ChunkInfo end{nullptr, -1, 0, 0, 0};
+        const ChunkInfo end{nullptr, nullptr, -1, 0, 0, 0, 0, 0u};
         int at, d;
         if (!begin(128, 0u, at, d, &end)) dead = true;
     }
@@ -455,37 +516,40 @@ __device__ void store_back(const BStepArgs &A, unsigned char *ring, uint64_t *wr
     const int L = A.L;
     int ds = 0;
     unsigned rph = 0;   // parity of the next `ready` wait, per descriptor
-    for (int item = blockIdx.x; item < A.n_items; item += gridDim.x) {
-        const BItem it = decode_item(A, item);
-        const BImage im = A.imgs[it.slot];
-        if (im.ctl->stop) continue;
-        const int P = im.pitch;
-        const int nwp = scale_row(im.W, L);
-        const int rows = it.nu * L;
-        ds = ds + 1 == kD ? 0 : ds + 1;   // the x chunk: released by the consumers
-        for (int b = 0; b < L; ++b) {
-            int ok = 1;
-            if (lane == 0) ok = wait_phase(&ready[ds], (rph >> ds) & 1u, A, s_abort) ? 1 : 0;
-            if (!__shfl_sync(0xffffffffu, ok, 0)) {
-                bulk_wait_all();
-                return;
+    for (int g = 0; g < A.n_groups; ++g) {
+        const BGroup G = A.groups[g];
+        for (int item = blockIdx.x; item < G.n_items; item += gridDim.x) {
+            const BItem it = decode_item(A, G, item);
+            const BImage im = A.imgs[it.slot];
+            if (im.ctl->stop) continue;
+            const int P = im.pitch;
+            const int nwp = scale_row(im.W, L);
+            const int rows = it.nu * L;
+            ds = ds + 1 == kD ? 0 : ds + 1;   // the x chunk: released by the consumers
+            for (int b = 0; b < L; ++b) {
+                int ok = 1;
+                if (lane == 0) ok = wait_phase(&ready[ds], (rph >> ds) & 1u, A, s_abort) ? 1 : 0;
+                if (!__shfl_sync(0xffffffffu, ok, 0)) {
+                    bulk_wait_all();
+                    return;
+                }
+                rph ^= 1u << ds;
+                const unsigned char *src = ring + s_off[ds];
+                QT *qdst = reinterpret_cast<QT *>(im.q) + im.qoff[G.p0 + b] + (size_t)it.u0 * L * P;
+                for (int r = lane; r < rows; r += 32) {
+                    const int s = r / L, i = r - s * L;
+                    bulk_store(qdst + (size_t)r * P, src + (size_t)(i * VW + s * P) * esz,
+                               (unsigned)(P * esz));
+                }
+                if (MIXED && lane == 0)
+                    bulk_store(im.qs + im.soff[G.p0 + b] + (size_t)it.u0 * nwp, src + (size_t)L * VW * esz,
+                               (unsigned)(it.nu * nwp) * 4u);
+                bulk_commit();
+                bulk_wait_read0();
+                __syncwarp();
+                if (lane == 0) mbar_arrive_cnt(&written[ds], kNCW);
+                ds = ds + 1 == kD ? 0 : ds + 1;
             }
-            rph ^= 1u << ds;
-            const unsigned char *src = ring + s_off[ds];
-            QT *qdst = reinterpret_cast<QT *>(im.q) + im.qoff[A.p0 + b] + (size_t)it.u0 * L * P;
-            for (int r = lane; r < rows; r += 32) {
-                const int s = r / L, i = r - s * L;
-                bulk_store(qdst + (size_t)r * P, src + (size_t)(i * VW + s * P) * esz,
-                           (unsigned)(P * esz));
-            }
-            if (MIXED && lane == 0)
-                bulk_store(im.qs + im.soff[A.p0 + b] + (size_t)it.u0 * nwp, src + (size_t)L * VW * esz,
-                           (unsigned)(it.nu * nwp) * 4u);
-            bulk_commit();
-            bulk_wait_read0();
-            __syncwarp();
-            if (lane == 0) mbar_arrive_cnt(&written[ds], kNCW);
-            ds = ds + 1 == kD ? 0 : ds + 1;
         }
     }
     bulk_wait_all();
@@ -769,12 +833,28 @@ __global__ void __launch_bounds__(kThreads, 1) bstep_kernel(const BStepArgs A)
                     if (i < L)
                         *reinterpret_cast<float2 *>(xg + og[j] + i * P) = x[i][j];
             }
+        if (A.n_groups > 1) {
+            // the item's window-rows are back: the next group's items that
+            // share rows with them may load them.  The barrier orders every
+            // consumer's stores before thread 0's release at GPU scope; the
+            // producer that acquires the flag fences its own proxy before the
+            // bulk loads.
+            named_sync(1, kNC);
+            if (tid == 0)
+                for (int u = 0; u < nu; ++u) st_release(info.uflag + info.u0 + u, info.tag);
+        }
     }
 }
 
 template <typename QT, int LB, bool EXACT>
 cudaError_t launch_step_t(const BStepArgs &A, int grid, size_t smem, cudaStream_t s)
 {
+    if (A.n_groups > 1) {
+        // items wait for items of other CTAs: every CTA must be resident
+        void *args[] = {const_cast<BStepArgs *>(&A)};
+        return cudaLaunchCooperativeKernel((const void *)bstep_kernel<QT, LB, EXACT>, dim3(grid),
+                                           dim3(kThreads), args, smem, s);
+    }
     bstep_kernel<QT, LB, EXACT><<<grid, kThreads, smem, s>>>(A);
     return cudaGetLastError();
 }

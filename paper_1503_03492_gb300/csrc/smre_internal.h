@@ -141,20 +141,33 @@ struct BImage {
     Control *ctl;
     double *hist;             // [2 * hist_cap] step and |x_prev| per cycle
     double *part;             // [2 * nchunks] norm partials of the current cycle
+    unsigned *uflag;          // [H] per window-row u of the running side: tag of the last
+                              // group (L, a) that wrote its rows back (one launch per side)
     int H, W, pitch, nchunks;
     int hist_cap, pad_;
 };
 
-// One launch of the step kernel: every item of group (L, a) over the batch.
-// An item is k consecutive units (k L rows) of one image, k * pitch <= the
-// kernel's virtual width.
+// One group (L, a) of a step launch: its items over the active images.
+struct BGroup {
+    const int *prefix;        // [n_active + 1] first item of each active image
+    const int *kpack;         // [n_active] units per item
+    int n_items;
+    int a, p0;                // row offset, plane of tiling (L, a, 0)
+    int seq;                  // place of the group in the cycle (flag tags)
+};
+
+// One launch of the step kernel: every item of n_groups consecutive groups
+// (L, a) of one side over the batch.  An item is k consecutive units (k L
+// rows) of one image, k * pitch <= the kernel's virtual width.  With more
+// than one group, an item waits for the items of the previous group of its
+// image whose rows it shares (per-image window-row flags; cooperative launch).
 struct BStepArgs {
     const BImage *imgs;
     const int *active;        // [n_active] slot of each active image
-    const int *prefix;        // [n_active + 1] first item of each active image
-    const int *kpack;         // [n_active] units per item
-    int n_active, n_items;
-    int L, a, p0;             // side, row offset, plane of tiling (L, a, 0)
+    const BGroup *groups;     // [n_groups] in cycle order
+    int n_active, n_groups;
+    int max_items;            // largest n_items of the groups
+    int L;                    // side
     float cS, sqrt_cS;
     double cS64;
     int ring_bytes;           // shared-memory ring for x and increment blocks

@@ -68,6 +68,22 @@ def test_repeated_side_needs_the_same_bound(smre):
     assert ei.value.status == smre.SMRE_EINVAL and "twice" in str(ei.value)
 
 
+def test_batch_schedule_flags_and_flag_rows(smre):
+    """Batch flags are validated on the host: SMRE_BF_PER_SIDE is accepted
+    alone and with a spread, an unknown bit or both spreads at once are not
+    (image_bytes answers 0 for invalid parameters), and no flag changes an
+    image's footprint."""
+    sides = [1, 2, 3, 8]
+    ok = [0, smre.SMRE_BF_PER_SIDE, smre.SMRE_BF_PER_SIDE | smre.SMRE_BF_SPREAD4,
+          smre.SMRE_BF_PER_SIDE | smre.SMRE_BF_AUTOTUNE]
+    sizes = {f: smre.smre_batch_image_bytes(smre.make_batch_params(sides, flags=f), 300, 200) for f in ok}
+    assert len(set(sizes.values())) == 1 and sizes[0] > 0        # flags do not change the layout
+    for bad in (16, smre.SMRE_BF_SPREAD2 | smre.SMRE_BF_SPREAD4, 1 << 20):
+        assert smre.smre_batch_image_bytes(smre.make_batch_params(sides, flags=bad), 300, 200) == 0, bad
+    # every part of the footprint, the flag row included, starts 256-byte aligned
+    assert sizes[0] % 256 == 0
+
+
 @pytest.mark.parametrize("kw,msg", [
     (dict(H=0, W=8, sides=[1]), "out of range"),
     (dict(H=8, W=5000, sides=[1]), "width"),

@@ -315,11 +315,13 @@ def test_autotuned_schedule_gives_the_same_answer(smre, torch_cuda, oracle_mod):
 
 @pytest.mark.parametrize("qdt", [0, 1])
 def test_item_spread_and_its_autotuner_give_the_same_bits(smre, oracle_mod, qdt):
-    """Items of a step cover every SM `spread` times (1, 2 or 4); the per-window
-    arithmetic and the norm chunks do not depend on it, so every spread -- and
-    the one SMRE_BF_AUTOTUNE picks by timing cycles of the run itself -- gives
-    the same images bit for bit.  A second batch of the same shapes takes the
-    tuned spread from the cache."""
+    """Items of a step cover every SM `spread` times (1, 2 or 4), and the
+    groups of a side run as one launch each or share one cooperative launch
+    (SMRE_BF_PER_SIDE, items waiting on per-image window-row flags); the
+    per-window arithmetic and the norm chunks depend on neither, so every
+    schedule -- and the one SMRE_BF_AUTOTUNE picks by timing cycles of the run
+    itself -- gives the same images bit for bit.  A second batch of the same
+    shapes takes the tuned schedule from the cache."""
     shapes = [(200, 300), (64, 64), (513, 257), (128, 1024), (90, 77)]
     xs = images(shapes, seed0=901)
     sides = [1, 2, 3, 5, 8]
@@ -327,7 +329,9 @@ def test_item_spread_and_its_autotuner_give_the_same_bits(smre, oracle_mod, qdt)
     kw = dict(cmode=smre.SMRE_C_EXPLICIT, c_explicit=list(cS), max_cycles=9, tol=-1.0,
               q_dtype=qdt, max_images=len(xs), device_bytes=1 << 30)
     runs = {}
+    side = smre.SMRE_BF_PER_SIDE
     for name, flags in (("1", 0), ("2", smre.SMRE_BF_SPREAD2), ("4", smre.SMRE_BF_SPREAD4),
+                        ("side1", side), ("side4", side | smre.SMRE_BF_SPREAD4),
                         ("tuned", smre.SMRE_BF_AUTOTUNE), ("cached", smre.SMRE_BF_AUTOTUNE)):
         outs = [np.full_like(x, np.nan) for x in xs]
         with smre.Batch(sides, flags=flags, **kw) as B:
@@ -337,15 +341,61 @@ def test_item_spread_and_its_autotuner_give_the_same_bits(smre, oracle_mod, qdt)
             done = B.poll()
             assert sorted(done) == sorted(slots)
             spread, tuned = B.item_spread()
+            per_side = B.per_side()
             for sl, o in zip(slots, outs):
                 B.retrieve(sl, o)
-        runs[name] = (outs, spread, tuned)
+        runs[name] = (outs, spread, tuned, per_side)
     assert (runs["1"][1], runs["2"][1], runs["4"][1]) == (1, 2, 4)
-    assert runs["tuned"][2] in (1, 2) and runs["tuned"][1] in (1, 2, 4)
-    assert runs["cached"][2] == 2 and runs["cached"][1] == runs["tuned"][1]
-    for name in ("2", "4", "tuned", "cached"):
+    assert not runs["1"][3] and runs["side1"][3] and runs["side4"][3]
+    assert (runs["side1"][1], runs["side4"][1]) == (1, 4)
+    assert runs["tuned"][2] in (1, 2) and runs["tuned"][1] in (1, 4)
+    assert runs["cached"][2] == 2 and runs["cached"][1:4:2] == runs["tuned"][1:4:2]
+    for name in ("2", "4", "side1", "side4", "tuned", "cached"):
         for a, b in zip(runs["1"][0], runs[name][0]):
             assert np.array_equal(a, b), name
+
+
+@pytest.mark.parametrize("qdt", [0, 2])
+def test_one_launch_per_side_with_stopping_and_joining(smre, oracle_mod, qdt):
+    """One cooperative launch per side (every group of the side, items waiting
+    for the window-rows they share with the previous group's items of their
+    image) against one launch per group: images of different sizes stop at
+    different cycles (relative tolerance), one joins between runs, sides
+    reach 16 (the run-time side build); every image ends bit for bit as under
+    the per-group launches, after the same number of cycles."""
+    shapes = [(300, 200), (48, 64), (257, 513), (96, 1024), (130, 130), (20, 24)]
+    xs = images(shapes, seed0=977)
+    late = images([(180, 240)], seed0=991)[0]
+    sides = [1, 2, 3, 4, 6, 9, 12, 16]
+    cS = oracle_mod.bounds(sides, 0.9)
+    kw = dict(cmode=smre.SMRE_C_EXPLICIT, c_explicit=list(cS), max_cycles=200, tol=1e-3,
+              tol_relative=True, q_dtype=qdt, max_images=len(xs) + 1, device_bytes=1 << 30)
+    runs = {}
+    for name, flags in (("group", 0), ("side", smre.SMRE_BF_PER_SIDE)):
+        res = {}
+        with smre.Batch(sides, flags=flags, **kw) as B:
+            slots = [B.submit(x) for x in xs]
+            assert all(sl >= 0 for sl in slots)
+            B.run(2)
+            sl_late = B.submit(late)
+            assert sl_late >= 0
+            order = slots + [sl_late]
+            for _ in range(40):
+                B.run(10)
+                for sl in B.poll():
+                    i = order.index(sl)
+                    o = np.full_like((xs + [late])[i], np.nan)
+                    r = B.retrieve(sl, o)
+                    res[i] = (o, r.cycles)
+                if len(res) == len(order):
+                    break
+            assert len(res) == len(order)
+        runs[name] = res
+    cycles = [runs["group"][i][1] for i in runs["group"]]
+    assert len(set(cycles)) > 1, cycles          # the images stopped at different cycles
+    for i in runs["group"]:
+        assert runs["side"][i][1] == runs["group"][i][1], i
+        assert np.array_equal(runs["side"][i][0], runs["group"][i][0]), i
 
 
 # ------------------------------------------------------ full workload sizes
