@@ -152,6 +152,7 @@ class Clocks:
 MEASURED_TRAFFIC = {
     "smre-gb300 0.8 (sm_103a)": (217.6e6, 433.1e6),
     "smre-gb300 0.9 (sm_103a)": (217.6e6, 433.1e6),
+    "smre-gb300 0.10 (sm_103a)": (217.6e6, 433.0e6),
 }
 
 # Warp instructions one incomplete projection of this workload executes
@@ -164,19 +165,26 @@ MEASURED_TRAFFIC = {
 ICD_WARP_INSTRUCTIONS = {
     "smre-gb300 0.8 (sm_103a)": 21737554,
     "smre-gb300 0.9 (sm_103a)": 21737554,
+    "smre-gb300 0.10 (sm_103a)": 21737554,
 }
 
 
 # DRAM traffic per cycle of the batched step kernels (all step launches of
 # one later cycle, one ncu capture each: profiles/bstep_kernel_uneven_batch.md),
-# per library version and workload: (bytes read, bytes written).  The writes
-# miss what each launch leaves dirty in L2 (ncu flushes caches between the
-# serialised launches), so the reads are the check against the algorithmic
-# bytes; both are reported.
+# per library version and workload: (bytes read, bytes written, launches the
+# capture used).  The writes miss what each launch leaves dirty in L2 (ncu
+# flushes caches between the serialised launches), so the reads are the check
+# against the algorithmic bytes; both are reported.
 BATCH_TRAFFIC = {
     "smre-gb300 0.9 (sm_103a)": {
-        ("uneven256", 0): (135.795e9, 133.457e9), ("uneven256", 1): (82.654e9, 80.306e9),
-        ("img2048", 0): (12.176e9, 7.194e9), ("img2048", 1): (6.949e9, 2.154e9),
+        ("uneven256", 0): (135.795e9, 133.457e9, "per group"),
+        ("uneven256", 1): (82.654e9, 80.306e9, "per group"),
+        ("img2048", 0): (12.176e9, 7.194e9, "per group"), ("img2048", 1): (6.949e9, 2.154e9, "per group"),
+    },
+    "smre-gb300 0.10 (sm_103a)": {
+        ("uneven256", 0): (135.798e9, 133.456e9, "per group"),
+        ("uneven256", 1): (82.652e9, 80.354e9, "per group"),
+        ("img2048", 0): (11.325e9, 11.312e9, "per side"), ("img2048", 1): (5.903e9, 5.797e9, "per side"),
     },
 }
 
@@ -193,7 +201,8 @@ def batch_traffic(smre, case, qdt, shapes, sides):
         return None
     inc = q_bytes_per_cycle(shapes, sides, qdt) - 8 * sum(h * w for h, w in shapes)
     xr = x_row_bytes_per_cycle(shapes, sides)
-    return {"read": t[0], "write": t[1], "algorithmic_increments": inc, "algorithmic_x_rows": xr,
+    return {"read": t[0], "write": t[1], "launches": t[2],
+            "algorithmic_increments": inc, "algorithmic_x_rows": xr,
             "read_over_algorithmic_read": t[0] / ((inc + xr) / 2),
             "note": "all step launches of one later cycle; writes miss what stays dirty in L2 "
                     "between the serialised launches"}
@@ -639,8 +648,12 @@ def main():
 
     x0 = make_input(1002 + rank)
     cS = smre.smre_bounds(smre.make_params(H, W, SIDES, alpha=ALPHA))
+    # the handle's schedule autotuner times every schedule that can run the
+    # shape (persistent launch, one-image batch, group launches) at create
     P = smre.Projector(H, W, SIDES, stream=stream, cmode=smre.SMRE_C_EXPLICIT, c_explicit=cS,
-                       max_cycles=MAX_CYCLES, tol=TOL, tol_relative=True)
+                       max_cycles=MAX_CYCLES, tol=TOL, tol_relative=True, flags=smre.SMRE_F_AUTOTUNE)
+    schedule = {smre.SMRE_SCHED_PERSISTENT: "persistent", smre.SMRE_SCHED_BATCHED: "one-image batch",
+                smre.SMRE_SCHED_GROUPS: "group launches"}.get(P.schedule(), "unknown")
     xd = torch.from_numpy(x0).to(dev)
     out_std = torch.empty_like(xd)
     out_icd = torch.empty_like(xd)
@@ -703,7 +716,7 @@ def main():
     avg_std = sum(std_s) / len(std_s)
     achieved = (sum(std_bytes) / len(std_bytes)) / avg_std / 1e9
     clocks = clk.summary()
-    tr = MEASURED_TRAFFIC.get(smre.smre_version())
+    tr = MEASURED_TRAFFIC.get(smre.smre_version()) if schedule == "persistent" else None
     cyc_med = int(np.median(cycles))
     traffic = None if tr is None else tr[0] + (cyc_med - 1) * tr[1]
     # the incomplete projection against its on-chip (issue-slot) ceiling
@@ -751,10 +764,12 @@ def main():
                        "standard_windows_per_step": std_windows // args.steps,
                        "icd_windows_per_step": icd_windows // args.steps,
                        "l2": "flushed between timed steps (256 MB write); q store 214 MB > L2",
+                       "schedule": schedule + " (SMRE_F_AUTOTUNE)",
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "persist_reg_kernel<8> (one launch = one standard projection)",
+                         "kernel": ("persist_reg_kernel<8> (one launch = one standard projection)"
+                                    if schedule == "persistent" else schedule),
                          "peak_source": peak_src,
                          "bytes_per_launch": sum(std_bytes) / len(std_bytes),
                          "seconds_per_launch": avg_std},

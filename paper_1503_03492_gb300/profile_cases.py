@@ -9,8 +9,9 @@
         a batch of copies of that image (one step-kernel launch per group);
     python -m paper_1503_03492_gb300.profile_cases uneven [--images 32] [--q bf16] [--cycles 2]
         the first images of the uneven 256-image batch (sides 128..1024, half 2:1);
-    python -m paper_1503_03492_gb300.profile_cases img2048 [--q bf16] [--cycles 2]
-        the 2048 x 2048 emitter residual with window sides 1..12 (batched path);
+    python -m paper_1503_03492_gb300.profile_cases img2048 [--q bf16] [--cycles 2] [--per-side]
+        the 2048 x 2048 emitter residual with window sides 1..12 (batched path;
+        --per-side: one cooperative launch per side, SMRE_BF_PER_SIDE);
     python -m paper_1503_03492_gb300.profile_cases admm512 [--iters 3] [--cycles 20]
         the ADMM outer loop on the same image (PSF sigma 2, 20 TV steps per
         iteration, a fixed number of projection cycles per eps-step).
@@ -38,6 +39,7 @@ def main(argv=None):
     ap.add_argument("--cycles", type=int, default=None)
     ap.add_argument("--images", type=int, default=None)
     ap.add_argument("--q", choices=list(QTYPES), default="fp32")
+    ap.add_argument("--per-side", action="store_true")
     a = ap.parse_args(argv)
 
     import torch
@@ -85,6 +87,7 @@ def main(argv=None):
                                                                   max_cycles=cycles), *x.shape)
                for x in xs)
     with smre.Batch(sides, cmode=smre.SMRE_C_EXPLICIT, c_explicit=cS, q_dtype=q,
+                    flags=smre.SMRE_BF_PER_SIDE if a.per_side else 0,
                     max_cycles=cycles, tol=-1.0, max_images=len(xs),
                     device_bytes=need + (64 << 20)) as B:
         for x in xs:
