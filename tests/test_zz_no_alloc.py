@@ -51,6 +51,11 @@ def test_static_entry_point_matches_allocating_path_twice(torch_cuda):
         assert r.cycles == r_ref.cycles == 25, (call, r.cycles, r_ref.cycles)
         e = _err(out.cpu().numpy(), ref.cpu().numpy())
         assert e <= TOL, (call, e)
+        # and against the FP64 oracle directly, at the same bar
+        import oracle
+        o = oracle.dykstra(x0.astype(np.float64), sides, list(cS), max_cycles=25, tol=-1).x
+        e64 = _err(out.cpu().numpy(), o)
+        assert e64 <= TOL, (call, e64)
 
 
 def test_static_entry_point_allocates_nothing_after_warm_up(torch_cuda):
