@@ -506,9 +506,33 @@ __device__ void produce(const BStepArgs &A, unsigned char *ring, uint64_t *full,
 // scales) into its chunk, copies each (unit, row) of the chunk to the
 // increment plane with bulk stores and releases the chunk to the producer
 // when every copy has read it.
+// Storer lane 0, several groups per launch: wait (bounded) until the
+// consumer warps have counted `need` stored items of x in *xdone.
+static __device__ __noinline__ bool wait_xdone(const BStepArgs &A, unsigned *xdone, unsigned need,
+                                               volatile int *s_abort)
+{
+    unsigned long long t0 = 0;
+    for (;;) {
+        unsigned v;
+        asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(smem_u32(xdone)) : "memory");
+        if ((int)(v - need) >= 0) return true;
+        if (*s_abort || ld_volatile(A.err)) break;
+        const unsigned long long t = globaltimer();
+        if (t0 == 0) {
+            t0 = t;
+        } else if (t - t0 > A.timeout_ns) {
+            atomicCAS(A.err, 0, (int)SMRE_ETIMEOUT);
+            break;
+        }
+        __nanosleep(64);
+    }
+    *s_abort = 1;
+    return false;
+}
+
 template <typename QT, int VW>
 __device__ void store_back(const BStepArgs &A, unsigned char *ring, uint64_t *written,
-                           uint64_t *ready, const int *s_off, volatile int *s_abort)
+                           uint64_t *ready, unsigned *xdone, const int *s_off, volatile int *s_abort)
 {
     constexpr bool MIXED = QConv<QT>::mixed;
     constexpr int esz = (int)sizeof(QT);
@@ -516,6 +540,7 @@ __device__ void store_back(const BStepArgs &A, unsigned char *ring, uint64_t *wr
     const int L = A.L;
     int ds = 0;
     unsigned rph = 0;   // parity of the next `ready` wait, per descriptor
+    unsigned xneed = 0;   // consumer-warp counts in *xdone of the items published so far
     for (int g = 0; g < A.n_groups; ++g) {
         const BGroup G = A.groups[g];
         for (int item = blockIdx.x; item < G.n_items; item += gridDim.x) {
@@ -550,6 +575,26 @@ __device__ void store_back(const BStepArgs &A, unsigned char *ring, uint64_t *wr
                 if (lane == 0) mbar_arrive_cnt(&written[ds], kNCW);
                 ds = ds + 1 == kD ? 0 : ds + 1;
             }
+            if (A.n_groups > 1) {
+                // several groups in this launch: once the consumers have
+                // stored the item's rows of x, its window-rows are released to
+                // the next group's items (one GPU-scope fence, cumulative over
+                // the consumers' stores seen through the count, then relaxed
+                // flag stores; the producer that acquires a flag fences its own
+                // proxy before the bulk loads)
+                int ok = 1;
+                xneed += kNCW;
+                if (lane == 0) ok = wait_xdone(A, xdone, xneed, s_abort) ? 1 : 0;
+                if (!__shfl_sync(0xffffffffu, ok, 0)) {
+                    bulk_wait_all();
+                    return;
+                }
+                if (lane == 0) {
+                    __threadfence();
+                    const unsigned tag = group_tag(im, G);
+                    for (int u = 0; u < it.nu; ++u) st_relaxed(im.uflag + it.u0 + u, tag);
+                }
+            }
         }
     }
     bulk_wait_all();
@@ -578,6 +623,8 @@ __global__ void __launch_bounds__(kThreads, 1) bstep_kernel(const BStepArgs A)
     unsigned char *ring = smem + A.ring_offset;
     __shared__ volatile int s_abort;
     __shared__ ChunkInfo s_info[kD];
+    __shared__ unsigned s_xdone;   // consumer warps that stored their rows of x, over all items
+    unsigned *xdone = &s_xdone;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int L = EXACT ? LB : A.L;
@@ -588,6 +635,7 @@ __global__ void __launch_bounds__(kThreads, 1) bstep_kernel(const BStepArgs A)
             mbar_init(&ready[d], kNCW);
             s_off[d] = 0;
         }
+        *xdone = 0u;
         fence_mbar_init();
         s_abort = 0;
     }
@@ -598,7 +646,7 @@ __global__ void __launch_bounds__(kThreads, 1) bstep_kernel(const BStepArgs A)
         return;
     }
     if (warp == kNCW + 1) {
-        store_back<QT, VW>(A, ring, written, ready, s_off, &s_abort);
+        store_back<QT, VW>(A, ring, written, ready, xdone, s_off, &s_abort);
         return;
     }
 
@@ -834,14 +882,12 @@ __global__ void __launch_bounds__(kThreads, 1) bstep_kernel(const BStepArgs A)
                         *reinterpret_cast<float2 *>(xg + og[j] + i * P) = x[i][j];
             }
         if (A.n_groups > 1) {
-            // the item's window-rows are back: the next group's items that
-            // share rows with them may load them.  The barrier orders every
-            // consumer's stores before thread 0's release at GPU scope; the
-            // producer that acquires the flag fences its own proxy before the
-            // bulk loads.
-            named_sync(1, kNC);
-            if (tid == 0)
-                for (int u = 0; u < nu; ++u) st_release(info.uflag + info.u0 + u, info.tag);
+            // the item's rows of x are stored: count this warp (release); the
+            // storer warp publishes the window-rows once every consumer warp
+            // has counted the item
+            __syncwarp();
+            if (lane == 0)
+                asm volatile("red.release.cta.shared::cta.add.u32 [%0], 1;" ::"r"(smem_u32(xdone)) : "memory");
         }
     }
 }
