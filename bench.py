@@ -153,6 +153,7 @@ MEASURED_TRAFFIC = {
     "smre-gb300 0.8 (sm_103a)": (217.6e6, 433.1e6),
     "smre-gb300 0.9 (sm_103a)": (217.6e6, 433.1e6),
     "smre-gb300 0.10 (sm_103a)": (217.6e6, 433.0e6),
+    "smre-gb300 0.11 (sm_103a)": (217.6e6, 433.1e6),
 }
 
 # Warp instructions one incomplete projection of this workload executes
@@ -166,6 +167,7 @@ ICD_WARP_INSTRUCTIONS = {
     "smre-gb300 0.8 (sm_103a)": 21737554,
     "smre-gb300 0.9 (sm_103a)": 21737554,
     "smre-gb300 0.10 (sm_103a)": 21737554,
+    "smre-gb300 0.11 (sm_103a)": 21737554,
 }
 
 
@@ -185,6 +187,11 @@ BATCH_TRAFFIC = {
         ("uneven256", 0): (135.798e9, 133.456e9, "per group"),
         ("uneven256", 1): (82.652e9, 80.354e9, "per group"),
         ("img2048", 0): (11.325e9, 11.312e9, "per side"), ("img2048", 1): (5.903e9, 5.797e9, "per side"),
+    },
+    "smre-gb300 0.11 (sm_103a)": {
+        ("uneven256", 0): (135.797e9, 133.457e9, "per group"),
+        ("uneven256", 1): (82.651e9, 80.306e9, "per group"),
+        ("img2048", 0): (11.321e9, 11.288e9, "per side"), ("img2048", 1): (5.899e9, 5.763e9, "per side"),
     },
 }
 
