@@ -154,6 +154,7 @@ MEASURED_TRAFFIC = {
     "smre-gb300 0.9 (sm_103a)": (217.6e6, 433.1e6),
     "smre-gb300 0.10 (sm_103a)": (217.6e6, 433.0e6),
     "smre-gb300 0.11 (sm_103a)": (217.6e6, 433.1e6),
+    "smre-gb300 0.12 (sm_103a)": (217.6e6, 433.1e6),
 }
 
 # Warp instructions one incomplete projection of this workload executes
@@ -168,6 +169,7 @@ ICD_WARP_INSTRUCTIONS = {
     "smre-gb300 0.9 (sm_103a)": 21737554,
     "smre-gb300 0.10 (sm_103a)": 21737554,
     "smre-gb300 0.11 (sm_103a)": 21737554,
+    "smre-gb300 0.12 (sm_103a)": 24523220,   # K = 3 at 4 pixels a thread
 }
 
 
@@ -193,6 +195,11 @@ BATCH_TRAFFIC = {
         ("uneven256", 1): (82.651e9, 80.306e9, "per group"),
         ("img2048", 0): (11.321e9, 11.288e9, "per side"), ("img2048", 1): (5.899e9, 5.763e9, "per side"),
     },
+    "smre-gb300 0.12 (sm_103a)": {
+        ("uneven256", 0): (135.797e9, 133.456e9, "per group"),
+        ("uneven256", 1): (82.652e9, 80.306e9, "per group"),
+        ("img2048", 0): (11.322e9, 11.287e9, "per side"), ("img2048", 1): (5.899e9, 5.762e9, "per side"),
+    },
 }
 
 
@@ -213,6 +220,28 @@ def batch_traffic(smre, case, qdt, shapes, sides):
             "read_over_algorithmic_read": t[0] / ((inc + xr) / 2),
             "note": "all step launches of one later cycle; writes miss what stays dirty in L2 "
                     "between the serialised launches"}
+
+
+def icd_critical_path(sweeps, H, W, K, seconds):
+    """The incomplete projection's passes run their tiles side by side, each
+    tile's sweeps one after another: a pass lasts as long as its tile with the
+    most sweeps.  sweeps: per-tile counts of the last call, pass by pass
+    (i = 0..K), tiles row-major; pass i covers the B x B tiles (B = 2^K) at
+    offset (1 << i) mod B that lie inside the image."""
+    B = 1 << K
+    counts = [((H - (1 << i) % B) // B) * ((W - (1 << i) % B) // B) for i in range(K + 1)]
+    if len(sweeps) != sum(counts):
+        return None
+    o, longest = 0, []
+    for i in range(K + 1):
+        n = counts[i]
+        longest.append(int(max(sweeps[o:o + n])) if n else 0)
+        o += n
+    crit = sum(longest)
+    return {"longest_tile_sweeps_per_pass": longest, "sweeps": crit,
+            "us_per_sweep_on_it": 1e6 * seconds / crit if crit else None,
+            "tiles_total_sweeps": int(sum(sweeps)),
+            "note": "a call takes at least its passes' longest tile chains of sweeps"}
 
 
 def measured_peak_hbm():
@@ -740,7 +769,8 @@ def main():
                     "peak_source": "warp instructions per call from ncu x (SMs x 4 issue slots x "
                                    "median SM clock)",
                     "warp_instructions_per_call": ins, "seconds_per_call": icd_sec,
-                    "hbm_bytes_per_call": 8 * H * W * (ICD_K + 1)}
+                    "hbm_bytes_per_call": 8 * H * W * (ICD_K + 1),
+                    "critical_path": icd_critical_path(P.icd_sweeps(), H, W, ICD_K, icd_sec)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -29,7 +29,10 @@ template <int K>
 struct IcdShape {
     static constexpr int B = 1 << K;
     static constexpr int NPX = B * B;
-    static constexpr int P = K <= 0 ? 1 : (K <= 3 ? 2 : 8);       // pixels per thread
+    // pixels per thread: K = 3 (8 x 8 tiles) takes 4 -- two tiles a warp, one
+    // shuffle step less per level-2 window and per sweep reduction than with
+    // 2 (512^2, K 3, tol 1e-3: 185 -> 177 us per call; 8 a thread, 222 us)
+    static constexpr int P = K <= 0 ? 1 : (K < 3 ? 2 : K == 3 ? 4 : 8);
     static constexpr int TPT = NPX / P;                               // threads per tile
     static constexpr int TPC = TPT >= 128 ? 1 : 128 / TPT;            // tiles per CTA
     static constexpr int THREADS = TPT * TPC;

@@ -66,3 +66,22 @@ def test_reference_arm_other_ranks_exit_quietly():
                         "--gpus", "2", "--steps", "1", "--warmup", "0"],
                        env=env, capture_output=True, text=True, timeout=120)
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_icd_critical_path_of_the_sweep_counts():
+    """bench.py's critical path of an incomplete projection: per pass the tile
+    with the most sweeps, over the pass's tile grid (offset (1 << i) mod B),
+    summed; a count list of the wrong length gives None."""
+    import numpy as np
+    import bench
+    H, W, K = 20, 27, 2                      # B = 4: offsets 1, 2, 0
+    counts = [((H - (1 << i) % 4) // 4) * ((W - (1 << i) % 4) // 4) for i in range(3)]
+    assert counts == [4 * 6, 4 * 6, 5 * 6]
+    sw = np.ones(sum(counts), np.int32)
+    sw[3] = 9                                # pass 0
+    sw[counts[0] + 5] = 4                    # pass 1
+    sw[-1] = 2                               # pass 2 (last tile)
+    r = bench.icd_critical_path(sw, H, W, K, 30e-6)
+    assert r["longest_tile_sweeps_per_pass"] == [9, 4, 2] and r["sweeps"] == 15
+    assert abs(r["us_per_sweep_on_it"] - 2.0) < 1e-12
+    assert bench.icd_critical_path(sw[:-1], H, W, K, 30e-6) is None
