@@ -962,7 +962,7 @@ cudaError_t host_malloc(void **p, size_t bytes)
 
 extern "C" {
 
-const char *smre_version(void) { return "smre-gb300 0.12 (sm_103a)"; }
+const char *smre_version(void) { return "smre-gb300 0.13 (sm_103a)"; }
 
 const char *smre_last_error(const smre_dykstra *h)
 {

@@ -917,16 +917,23 @@ __global__ void __launch_bounds__((NW + 2) * 32, 1) persist_reg_kernel(const __g
         for (int si = 0; si < nside && !aborted; ++si) {
             const SideS &sd = sides_s[si];
             // side start: wait for the same warp of the last publishers of the
-            // band's rows (or a self-test flag nothing sets)
-            if (lane == 0 && !lost) {
-                bool ok = true;
-                if (A.selftest_timeout && cta == 0 && si == 0 && warp == 0)
-                    ok = wait_geq(A, A.selftest_flag, 1u);
-                for (int k = 0; k < sd.dep_count && ok; ++k)
-                    ok = wait_geq(A, A.flags + (size_t)deps_s[sd.dep_begin + k] * NCW + warp, want);
+            // band's rows (or a self-test flag nothing sets), one publisher a
+            // lane, so flags already set cost one round trip, not one each;
+            // the __syncwarp orders every lane's acquire before the band loads
+            lost = __any_sync(kFull, lost);
+            if (!lost) {
+                int ok = 1;
+                if (lane == 0 && A.selftest_timeout && cta == 0 && si == 0 && warp == 0)
+                    ok = wait_geq(A, A.selftest_flag, 1u) ? 1 : 0;
+                ok = __shfl_sync(kFull, ok, 0);
+                for (int k0 = 0; ok && k0 < sd.dep_count; k0 += 32) {
+                    const int k = k0 + lane;
+                    const bool mine = k >= sd.dep_count ||
+                                      wait_geq(A, A.flags + (size_t)deps_s[sd.dep_begin + k] * NCW + warp, want);
+                    ok = __all_sync(kFull, mine) ? 1 : 0;
+                }
                 lost = !ok;
             }
-            lost = __shfl_sync(kFull, lost ? 1 : 0, 0) != 0;
             __syncwarp();
             // one dispatch per side: the band lives inside the side's own code
             switch (sd.L) {
