@@ -155,6 +155,7 @@ MEASURED_TRAFFIC = {
     "smre-gb300 0.10 (sm_103a)": (217.6e6, 433.0e6),
     "smre-gb300 0.11 (sm_103a)": (217.6e6, 433.1e6),
     "smre-gb300 0.12 (sm_103a)": (217.6e6, 433.1e6),
+    "smre-gb300 0.13 (sm_103a)": (217.6e6, 433.2e6),
 }
 
 # Warp instructions one incomplete projection of this workload executes
@@ -170,6 +171,7 @@ ICD_WARP_INSTRUCTIONS = {
     "smre-gb300 0.10 (sm_103a)": 21737554,
     "smre-gb300 0.11 (sm_103a)": 21737554,
     "smre-gb300 0.12 (sm_103a)": 24523220,   # K = 3 at 4 pixels a thread
+    "smre-gb300 0.13 (sm_103a)": 24523220,
 }
 
 
@@ -199,6 +201,11 @@ BATCH_TRAFFIC = {
         ("uneven256", 0): (135.797e9, 133.456e9, "per group"),
         ("uneven256", 1): (82.652e9, 80.306e9, "per group"),
         ("img2048", 0): (11.322e9, 11.287e9, "per side"), ("img2048", 1): (5.899e9, 5.762e9, "per side"),
+    },
+    "smre-gb300 0.13 (sm_103a)": {
+        ("uneven256", 0): (135.797e9, 133.457e9, "per group"),
+        ("uneven256", 1): (82.652e9, 80.306e9, "per group"),
+        ("img2048", 0): (11.326e9, 11.290e9, "per side"), ("img2048", 1): (5.901e9, 5.767e9, "per side"),
     },
 }
 
